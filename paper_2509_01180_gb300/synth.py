@@ -1,0 +1,175 @@
+"""Seeded synthetic workloads: blob phantoms, rotations, noise, missing wedge, random starts.
+
+This module is the one piece of input preparation that the CUDA path and the
+FP64 oracle both use.  It contains none of the alignment method's arithmetic
+(no basis, no expansion, no Wigner matrices, no score): it only draws random
+numbers and renders test volumes.
+
+Synthetic data stand in for the SHREC 2020 simulated tomograms the paper
+evaluates on (Sec. III); no SHREC item is reproduced.  Recipe:
+  * template: ``n_blobs`` isotropic Gaussians exp(-|p - c|^2 / (2 sigma^2)) in
+    voxel units, centres uniform in volume inside radius 0.75 * N/2 around the
+    box centre N/2, amplitudes U[0.5, 1];
+  * subtomogram p: the template rotated by a uniform random rotation R_p
+    (rendered analytically at R_p c, no interpolation), so f_p = R_p t with
+    (R t)(x) = t(R^{-1} x);
+  * optional white Gaussian noise with SNR = var(signal in the ball) / sigma_n^2,
+    added before the wedge mask;
+  * optional missing wedge about the y axis (beam along z): Fourier components
+    with |k_z| > tan(theta_max) |k_x| are zeroed, the k_x = k_z = 0 line kept;
+  * starts: uniform random rotations (Shoemake's method), per particle.
+Seeds: master seed 2509; the generator of particle i is seeded with
+splitmix64(master + i).  Volumes are float32 in [z][y][x] order; quaternions
+(w, x, y, z) are float32, and the FP64 oracle reads the same float32 values.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MASTER_SEED = 2509
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """One output of the SplitMix64 generator (Steele, Lea, Flood 2014) for state x."""
+    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def rng_for(stream: int, index: int, master: int = MASTER_SEED) -> np.random.Generator:
+    """Independent generator for (stream, index); streams separate templates, particles and starts."""
+    return np.random.default_rng(splitmix64((master * 1000003 + stream * 7919 + index) & _M64))
+
+
+def uniform_quaternions(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n uniform random unit quaternions (w, x, y, z), Shoemake's subgroup algorithm; w >= 0."""
+    u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    q = np.stack([b * np.cos(2 * np.pi * u3), a * np.sin(2 * np.pi * u2), a * np.cos(2 * np.pi * u2),
+                  b * np.sin(2 * np.pi * u3)], axis=1)
+    q *= np.where(q[:, :1] < 0, -1.0, 1.0)
+    return q
+
+
+def _rotation_matrix(q) -> np.ndarray:
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+@dataclass
+class BlobTemplate:
+    centres: np.ndarray  # (n, 3) voxel units relative to the box centre, (x, y, z)
+    amps: np.ndarray  # (n,)
+    sigma: float
+
+
+def blob_template(rng: np.random.Generator, n_blobs: int, sigma: float, r_max: float) -> BlobTemplate:
+    """Blob centres uniform in volume in the ball of radius r_max (voxels), amplitudes U[0.5, 1]."""
+    d = rng.normal(size=(n_blobs, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = r_max * rng.random(n_blobs) ** (1.0 / 3.0)
+    return BlobTemplate(d * r[:, None], 0.5 + 0.5 * rng.random(n_blobs), float(sigma))
+
+
+def render(N: int, tpl: BlobTemplate, q=None) -> np.ndarray:
+    """Volume vol[z, y, x] of the blobs (rotated by q when given), centre at voxel N/2 along each axis."""
+    c = tpl.centres if q is None else tpl.centres @ _rotation_matrix(q).T
+    p = np.arange(N, dtype=np.float64) - N / 2
+    s2 = 2.0 * tpl.sigma ** 2
+    ex = np.exp(-(p[None, :] - c[:, 0:1]) ** 2 / s2) * tpl.amps[:, None]
+    ey = np.exp(-(p[None, :] - c[:, 1:2]) ** 2 / s2)
+    ez = np.exp(-(p[None, :] - c[:, 2:3]) ** 2 / s2)
+    zy = (ez[:, :, None] * ey[:, None, :]).reshape(len(c), N * N)
+    return (zy.T @ ex).reshape(N, N, N)
+
+
+def ball_mask(N: int) -> np.ndarray:
+    h = N // 2
+    i = np.arange(N) - h
+    z, y, x = np.meshgrid(i, i, i, indexing="ij")
+    return (x * x + y * y + z * z) < h * h
+
+
+def wedge_mask(N: int, half_angle_deg: float) -> np.ndarray:
+    """Fourier mask keeping |k_z| <= tan(theta) |k_x| (tilt axis y, beam z) plus the k_x = k_z = 0 line."""
+    k = np.fft.fftfreq(N)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    keep = np.abs(kz) <= math.tan(math.radians(half_angle_deg)) * np.abs(kx) + 1e-12
+    keep |= (kx == 0) & (kz == 0)
+    return keep
+
+
+def degrade(vol: np.ndarray, rng: np.random.Generator, snr: float | None, wedge_deg: float | None) -> np.ndarray:
+    """Add white noise at the given SNR (signal variance inside the ball) and apply the missing wedge."""
+    out = vol
+    if snr is not None:
+        var = float(np.var(vol[ball_mask(vol.shape[0])]))
+        out = out + rng.normal(scale=math.sqrt(var / snr), size=vol.shape)
+    if wedge_deg is not None:
+        out = np.fft.ifftn(np.fft.fftn(out) * wedge_mask(vol.shape[0], wedge_deg)).real
+    return out
+
+
+@dataclass
+class Workload:
+    """One alignment workload: a template, B subtomograms and S starts per subtomogram."""
+
+    name: str
+    N: int
+    Lmax: int
+    lam_max: float
+    stages: list
+    steps: int
+    S: int
+    template: np.ndarray  # (N, N, N) float32
+    vols: np.ndarray  # (B, N, N, N) float32
+    q_true: np.ndarray  # (B, 4) float64: f_p = R(q_true[p]) t
+    starts: np.ndarray  # (B, S, 4) float32
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def B(self) -> int:
+        return self.vols.shape[0]
+
+
+# name: (N, Lmax, blobs, sigma, snr, wedge, stages, steps, starts, count)
+CONFIGS = {
+    # FP64 plain method, one noiseless pair (16^3, l <= 8, marching 2-4-8, 8 starts, 50 steps)
+    "pair16": (16, 8, 20, 1.2, None, None, [2, 4, 8], 50, 8, 1),
+    # FP32 plain method on the GPU: 1024 x 32^3, SNR 0.1, +-60 deg wedge, l <= 16, 4-8-16, 16 starts, 30 steps
+    "batch32": (32, 16, 60, 1.5, 0.1, 60.0, [4, 8, 16], 30, 16, 1024),
+    # precision form: 4096 x 64^3, SNR 0.05, +-60 deg, l <= 32, 4-8-16-32, 32 starts, 30 steps
+    "precision64": (64, 32, 200, 2.0, 0.05, 60.0, [4, 8, 16, 32], 30, 32, 4096),
+}
+
+
+def make_workload(name: str, count: int | None = None, first: int = 0, master: int = MASTER_SEED,
+                  snr=..., wedge=..., dtype=np.float32) -> Workload:
+    """Build particles first .. first+count-1 of a named workload (all deterministic in the seeds)."""
+    N, Lmax, nb, sigma, snr0, wedge0, stages, steps, S, B = CONFIGS[name]
+    snr = snr0 if snr is ... else snr
+    wedge = wedge0 if wedge is ... else wedge
+    count = B if count is None else count
+    tpl = blob_template(rng_for(1, 0, master), nb, sigma, 0.75 * N / 2)
+    template = render(N, tpl).astype(dtype)
+    vols = np.empty((count, N, N, N), dtype=dtype)
+    q_true = np.empty((count, 4))
+    starts = np.empty((count, S, 4), dtype=np.float32)
+    for j in range(count):
+        p = first + j
+        rng = rng_for(2, p, master)
+        q = uniform_quaternions(rng, 1)[0]
+        q_true[j] = q
+        vols[j] = degrade(render(N, tpl, q), rng, snr, wedge).astype(dtype)
+        starts[j] = uniform_quaternions(rng_for(3, p, master), S).astype(np.float32)
+    return Workload(name, N, Lmax, math.pi * N / 2, list(stages), steps, S, template, vols, q_true, starts,
+                    {"blobs": nb, "sigma": sigma, "snr": snr, "wedge_deg": wedge, "first": first})

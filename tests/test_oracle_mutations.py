@@ -1,0 +1,75 @@
+"""Planted mistakes: each plausible error in the oracle must fail one of its pins (CPU only).
+
+The mistakes are planted in the oracle (monkeypatched), never in the CUDA path."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import align, ball, wigner
+from tests import test_oracle_align as ta
+from tests import test_oracle_basis as tb
+from tests import test_oracle_wigner as tw
+
+
+def _fails(fn, *a):
+    try:
+        fn(*a)
+    except AssertionError:
+        return True
+    return False
+
+
+@pytest.mark.parametrize("mutant", ["transpose", "conjugate", "inverse"])
+def test_steerability_pin_catches_wrong_D_convention(monkeypatch, mutant):
+    orig = wigner.wigner_D
+
+    def bad(l, q):
+        D = orig(l, q)
+        return {"transpose": D.T, "conjugate": D.conj(), "inverse": D.conj().T}[mutant]
+
+    monkeypatch.setattr(wigner, "wigner_D", bad)
+    monkeypatch.setattr(align, "wigner_D", bad)
+    assert _fails(tw.test_steerability_exact_rotation)
+
+
+def test_gradient_pin_catches_sign_error(monkeypatch):
+    orig = wigner._j
+
+    def bad(l):
+        Jx, Jy, Jz = orig(l)
+        return Jx, -Jy, Jz
+
+    monkeypatch.setattr(align, "_j", bad)
+    Bs = ball.make_basis(4, 5 * math.pi)
+    rng = np.random.default_rng(1)
+    small = (Bs, rng.normal(size=Bs.Nb) + 1j * rng.normal(size=Bs.Nb), rng.normal(size=Bs.Nb) + 1j * rng.normal(size=Bs.Nb))
+    assert _fails(ta.test_gradient_matches_central_differences, small)
+
+
+def test_orthonormality_pin_catches_wrong_constant(monkeypatch):
+    monkeypatch.setattr(ball, "norm_const", lambda l, lam: 1.0 / abs(float(ball.sph_jn(l + 1, lam))))
+    assert _fails(tb.test_ball_basis_orthonormal)
+
+
+def test_ylm_pin_catches_missing_condon_shortley_phase(monkeypatch):
+    orig = ball.assoc_legendre_normalized
+
+    def bad(L, x):
+        P = orig(L, x)
+        for m in range(L + 1):
+            P[:, m] *= (-1) ** m
+        return P
+
+    monkeypatch.setattr(ball, "assoc_legendre_normalized", bad)
+    assert _fails(tb.test_ylm_closed_forms)
+
+
+def test_xi_pin_catches_swapped_conjugation(monkeypatch):
+    orig = align.build_xi
+
+    def bad(basis, t, f, L=None):
+        return orig(basis, np.conj(t), np.conj(f), L)
+
+    monkeypatch.setattr(align, "build_xi", bad)
+    assert _fails(ta.test_score_is_eq1_inner_product_of_rotated_volume)
