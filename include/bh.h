@@ -1,0 +1,178 @@
+/*
+ * bh.h -- C ABI of libbh: ball-harmonic expansion and rotational matching on one GB300 GPU.
+ *
+ * The library computes the two data-parallel stages of "Beyond Exhaustive Sampling: Efficient
+ * Rotational Matching via Ball Harmonics":
+ *
+ *   1. expansion of voxel volumes into ball-harmonic coefficients f_hat_klm on the basis
+ *      psi_klm = c_lk j_l(lambda_lk r) Y_l^m(theta, phi) chi_[0,1)(r)   (Sec. II-A), and
+ *   2. maximisation over rotations g of the rotational cross-correlation of Eq. 2 at shift s = 0,
+ *      C(g) = sum_{l<=L} sum_{m,m'} xi_{l,m,m'} D^l_{m,m'}(g), with its closed-form gradient,
+ *      multi-start gradient ascent and frequency marching (Sec. II-C).
+ *
+ * Conventions (all calls):
+ *   - Every call returns an int status: BH_OK (0), BH_PENDING (1, serving poll only) or a
+ *     negative BH_ERR_* code.  bh_last_error() returns a thread-local description of the last
+ *     failure on the calling thread.
+ *   - Array arguments documented as "device" are device pointers owned by the caller (for
+ *     example allocated by PyTorch); the library never frees them.  "host" arrays are ordinary
+ *     host memory.  Handles (bh_plan, bh_server) are created and destroyed by the library.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Device work is
+ *     enqueued asynchronously on it; the call returns once the work is queued.  Argument errors
+ *     are reported before anything is enqueued.
+ *   - Volumes are float32, layout vol[b][z][y][x] (x fastest), box edge N (even).  Voxel i on an
+ *     axis sits at (i - N/2)/(N/2) in unit-ball coordinates; the ball is the set of voxels with
+ *     (ix-N/2)^2 + (iy-N/2)^2 + (iz-N/2)^2 < (N/2)^2.
+ *   - Coefficients are complex64 stored as interleaved float pairs (re, im), layout
+ *     [b][l][k][m+l] for l = 0..Lmax, k = 0..K_l-1, m = -l..l; degree l starts at offsets[l]
+ *     (bh_plan_layout).  They are the discrete inner product
+ *     f_hat_klm = h^3 sum_{voxels in ball} f(x_v) conj(psi_klm(x_v)), h = 2/N, with
+ *     c_lk = sqrt(2)/|j_{l+1}(lambda_lk)| (orthonormal psi) and complex Y_l^m with the
+ *     Condon-Shortley phase.  Coefficients of real volumes satisfy
+ *     f_hat_{k,l,-m} = (-1)^m conj(f_hat_klm); the matching calls rely on this symmetry.
+ *   - Rotations are unit quaternions (w, x, y, z) in float32, the rotation by angle t about
+ *     axis n being (cos t/2, sin t/2 n).  A rotation acts on volumes by (R f)(x) = f(R^{-1} x)
+ *     and on coefficients by D^l_{mm'}(R) = <Y_l^m, R Y_l^m'>.  The score of R is
+ *     <t, R f> = Re sum_l sum_{m,m'} xi^l_{mm'} D^l_{mm'}(R),  xi^l_{mm'} = sum_k conj(t_klm) f_klm'
+ *     (Eq. 1 at s = 0 and Eq. 2).  When f = R_true t the maximiser is R_true^{-1}.
+ *   - The gradient is taken along right perturbations R exp(eps J_i) about the body axes
+ *     i = x, y, z.
+ */
+#ifndef BH_H
+#define BH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define BH_OK 0
+#define BH_PENDING 1          /* serving: the request is not finished yet */
+#define BH_ERR_ARG (-1)       /* invalid argument (NULL pointer, size out of range, bad option) */
+#define BH_ERR_CUDA (-2)      /* a CUDA runtime or driver call failed; the message names it */
+#define BH_ERR_OOM (-3)       /* device or host allocation failed */
+#define BH_ERR_BUDGET (-4)    /* serving: the request can never fit the HBM budget */
+#define BH_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up; results are invalid */
+#define BH_ERR_BUSY (-6)      /* serving: queue full, try again */
+#define BH_ERR_UNSUPPORTED (-7) /* the device or configuration is not supported (not sm_103) */
+
+/* expansion arithmetic (bh_plan_opts.mode) */
+#define BH_MODE_FP32 0        /* plain FP32 FFMA GEMM */
+#define BH_MODE_BF16_SPLIT 1  /* tcgen05 BF16 tensor-core GEMM, hi/lo split: Xh*Th + Xh*Tl + Xl*Th, FP32 accum */
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* bh_last_error(void);
+/* Static name of a status code. */
+const char* bh_status_string(int status);
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int bh_version(void);
+
+/* ------------------------------------------------------------------ host-only basis data */
+/*
+ * Radial data of the index set I = {(k,l,m): l <= Lmax, lambda_lk <= lambda_max} (Sec. II-A:
+ * lambda_lk is the k-th positive root of j_l; c_lk the positive normalisation constant).
+ * Computed in FP64 on the host; no GPU is touched.
+ *   Lmax        0..64
+ *   lambda_max  > 0; <= 0 is invalid here.  A root is kept when lambda_lk <= lambda_max + 1e-9.
+ *   K           host, Lmax+1 ints: K[l] = number of roots kept for degree l.
+ *   lambda, c   host, capacity `cap` doubles each, filled degree by degree (l = 0..Lmax, k ascending).
+ * Returns BH_ERR_ARG if cap is smaller than sum_l K[l] (K is still filled).
+ */
+int bh_basis_roots(int Lmax, double lambda_max, int* K, double* lambda, double* c, int cap);
+
+/* ------------------------------------------------------------------ plans */
+typedef struct bh_plan bh_plan;
+
+typedef struct {
+  int N;             /* box edge in voxels: even, 4..256 */
+  int Lmax;          /* largest degree: 0..64 */
+  double lambda_max; /* radial cutoff; <= 0 selects pi * N / 2 */
+  int mode;          /* BH_MODE_FP32 or BH_MODE_BF16_SPLIT */
+  int max_batch;     /* volumes per internal expansion pass (sizes the scratch); <= 0 selects 512 */
+} bh_plan_opts;
+
+/*
+ * Build a plan on the current CUDA device: roots and constants in FP64 on the host, the basis
+ * table Psi[j][v] (real form, one row per coefficient slot, h^3 folded in) evaluated in FP64
+ * and stored on the device in the arithmetic of `mode`, plus the expansion scratch.
+ * The plan owns all of its device memory.  Creation is synchronous.
+ * Errors: BH_ERR_ARG (options), BH_ERR_OOM, BH_ERR_CUDA, BH_ERR_UNSUPPORTED (device is not
+ * compute capability 10.3).
+ */
+int bh_plan_create(bh_plan** out, const bh_plan_opts* opts);
+/* Free the plan (synchronises the device first).  NULL is accepted. */
+int bh_plan_destroy(bh_plan* plan);
+/*
+ * Layout of the plan's coefficient vectors: *Nb = number of complex coefficients per volume,
+ * *V = number of voxels inside the ball, offsets (host, Lmax+2 ints, may be NULL) with
+ * offsets[l] = first slot of degree l and offsets[Lmax+1] = Nb.  Any output may be NULL.
+ */
+int bh_plan_layout(const bh_plan* plan, int* Nb, int* V, int* offsets);
+/* Options the plan was created with (lambda_max resolved). */
+int bh_plan_info(const bh_plan* plan, bh_plan_opts* opts);
+
+/* ------------------------------------------------------------------ expansion */
+/*
+ * Expansion display of Sec. II-A on the voxel grid: coeffs[b] = f_hat of vols[b].
+ *   vols    device, B * N^3 floats, layout [b][z][y][x].
+ *   B       >= 0 (0 is a no-op).
+ *   coeffs  device, B * Nb * 2 floats (complex interleaved), layout [b][l][k][m+l].
+ * Uses the plan's scratch: calls on one plan must be serialised (same stream or synchronised).
+ */
+int bh_expand(bh_plan* plan, const float* vols, int B, float* coeffs, void* stream);
+
+/* ------------------------------------------------------------------ score and gradient */
+/*
+ * Eq. 2 at s = 0, truncated at band L, and its closed-form gradient (Sec. II-C) at given
+ * rotations, one template against B subtomograms.
+ *   tmpl    device, Nb complex: template coefficients t_hat.
+ *   sub     device, B * Nb complex: subtomogram coefficients f_hat (real volumes).
+ *   quats   device, B * S * 4 floats: rotations, [b][s][w,x,y,z]; normalised internally.
+ *   S       1..512 rotations per subtomogram.
+ *   L       band, 0..Lmax.
+ *   score   device, B * S floats: Re sum_{l<=L} sum_{m,m'} xi^l_{mm'} D^l_{mm'}(R).
+ *   grad    device, B * S * 3 floats or NULL: d score(R exp(eps J_i))/d eps at 0, i = x, y, z.
+ */
+int bh_score_grad(const bh_plan* plan, const float* tmpl, const float* sub, int B,
+                  const float* quats, int S, int L, float* score, float* grad, void* stream);
+
+/* ------------------------------------------------------------------ alignment */
+typedef struct {
+  int group;              /* lanes cooperating on one start: 0 = autotuned, else 1, 2, 4, 8 or 16 */
+  const int* tmpl_index;  /* device, B ints selecting a template row of `tmpl`, or NULL (row 0) */
+  int n_templates;        /* rows in `tmpl` when tmpl_index is given */
+  float* start_quat_out;  /* device, B * S * 4 floats or NULL: final rotation of every start */
+  float* start_score_out; /* device, B * S floats or NULL: final score of every start */
+  int refine_fp64;        /* 1: re-score every start's final rotation in FP64 at the last band and
+                             select on those scores (score_out then holds the FP64 score) */
+} bh_align_opts;
+
+/*
+ * Multi-start gradient ascent with frequency marching (Sec. II-C) for B subtomograms, in one
+ * launch.  For every subtomogram and start: for each band L in `stages` (ascending, 1..Lmax):
+ * h = pi/(2L), evaluate score and gradient, then `steps` times: stop if |g| <= 1e-12 |S|; else
+ * u = g/|g|, trial R' = R exp(h u.J); accept if score(R') > score(R) (h <- min(1.5h, pi/L)),
+ * else h <- h/2.  The result of a subtomogram is the start with the largest final score
+ * (exact ties: lowest start index).
+ *   tmpl       device, Nb complex (or n_templates * Nb with opts->tmpl_index).
+ *   sub        device, B * Nb complex.
+ *   starts     device, B * S * 4 floats: initial rotations.
+ *   S          1..512 starts per subtomogram; S * group <= 512.
+ *   stages     host, nstages ints (1..8 stages), strictly increasing, each in 1..Lmax.
+ *   steps      ascent steps per stage, 0..100000.
+ *   quat_out   device, B * 4 floats: best rotation R* (maximiser of <t, R f>).
+ *   score_out  device, B floats: its score.
+ *   opts       may be NULL (all defaults).
+ */
+int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int B,
+                   const float* starts, int S, const int* stages, int nstages, int steps,
+                   float* quat_out, float* score_out, const bh_align_opts* opts, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BH_H */

@@ -1,0 +1,210 @@
+"""Thin Python binding of libbh (ctypes).  Argument marshalling only: every step runs in the library.
+
+Names follow the C ABI in include/bh.h.  Device arrays are torch CUDA tensors (PyTorch provides device
+memory and streams only); the library must be built in-tree (``paper_2509_01180_gb300/libbh.so``) and
+there is no fallback: a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbh.so")
+
+BH_OK, BH_PENDING = 0, 1
+BH_ERR_ARG, BH_ERR_CUDA, BH_ERR_OOM, BH_ERR_BUDGET, BH_ERR_TIMEOUT, BH_ERR_BUSY, BH_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
+
+# every symbol include/bh.h declares (checked by the CPU tests)
+EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
+           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_score_grad", "bh_align_batch"]
+
+
+class BHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("Lmax", ctypes.c_int), ("lambda_max", ctypes.c_double),
+                ("mode", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class AlignOpts(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int), ("tmpl_index", ctypes.c_void_p), ("n_templates", ctypes.c_int),
+                ("start_quat_out", ctypes.c_void_p), ("start_score_out", ctypes.c_void_p),
+                ("refine_fp64", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libbh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2509_01180_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.bh_last_error.restype = ctypes.c_char_p
+        L.bh_status_string.restype = ctypes.c_char_p
+        L.bh_status_string.argtypes = [i]
+        L.bh_version.restype = i
+        L.bh_basis_roots.argtypes = [i, d, vp, vp, vp, i]
+        L.bh_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PlanOpts)]
+        L.bh_plan_destroy.argtypes = [vp]
+        L.bh_plan_layout.argtypes = [vp, vp, vp, vp]
+        L.bh_plan_info.argtypes = [vp, ctypes.POINTER(PlanOpts)]
+        L.bh_expand.argtypes = [vp, vp, i, vp, vp]
+        L.bh_score_grad.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp]
+        L.bh_align_batch.argtypes = [vp, vp, vp, i, vp, i, vp, i, i, vp, vp, ctypes.POINTER(AlignOpts), vp]
+        for name in EXPORTS:
+            if name not in ("bh_last_error", "bh_status_string"):
+                getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        msg = lib().bh_last_error().decode(errors="replace")
+        raise BHError(status, f"{what}: {msg or lib().bh_status_string(status).decode()}")
+    return status
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _need(t, dtype_name: str, numel: int, what: str):
+    if t is None:
+        raise ValueError(f"{what} is required")
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != dtype_name or t.numel() < numel:
+        raise ValueError(f"{what}: need a contiguous CUDA {dtype_name} tensor with >= {numel} elements, "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+
+# ------------------------------------------------------------------ host-only basis data
+def bh_basis_roots(Lmax: int, lambda_max: float):
+    """(K, lambda, c) of the index set, FP64 on the host (no GPU)."""
+    K = np.zeros(Lmax + 1, dtype=np.int32)
+    cap = 1 << 16
+    lam = np.zeros(cap)
+    c = np.zeros(cap)
+    _check(lib().bh_basis_roots(Lmax, float(lambda_max), K.ctypes.data, lam.ctypes.data, c.ctypes.data, cap),
+           "bh_basis_roots")
+    n = int(K.sum())
+    return K, lam[:n].copy(), c[:n].copy()
+
+
+# ------------------------------------------------------------------ plans
+class Plan:
+    """Owns a bh_plan handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        o = PlanOpts()
+        _check(lib().bh_plan_info(handle, ctypes.byref(o)), "bh_plan_info")
+        self.N, self.Lmax, self.lambda_max, self.mode, self.max_batch = o.N, o.Lmax, o.lambda_max, o.mode, o.max_batch
+        Nb, V = ctypes.c_int(), ctypes.c_int()
+        offs = np.zeros(self.Lmax + 2, dtype=np.int32)
+        _check(lib().bh_plan_layout(handle, ctypes.addressof(Nb), ctypes.addressof(V), offs.ctypes.data),
+               "bh_plan_layout")
+        self.Nb, self.V, self.offsets = Nb.value, V.value, offs
+
+    def destroy(self):
+        if self.handle:
+            lib().bh_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def bh_plan_create(N: int, Lmax: int, lambda_max: float = 0.0, mode: int = BH_MODE_FP32, max_batch: int = 0) -> Plan:
+    o = PlanOpts(N, Lmax, float(lambda_max), mode, max_batch)
+    h = ctypes.c_void_p()
+    _check(lib().bh_plan_create(ctypes.byref(h), ctypes.byref(o)), "bh_plan_create")
+    return Plan(h.value)
+
+
+def bh_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def bh_plan_layout(plan: Plan):
+    return plan.Nb, plan.V, plan.offsets.copy()
+
+
+# ------------------------------------------------------------------ expansion
+def bh_expand(plan: Plan, vols, coeffs=None, stream=None):
+    """vols: CUDA float32 (B, N, N, N); returns coeffs: CUDA float32 (B, Nb, 2) (complex interleaved)."""
+    import torch
+    B = vols.shape[0]
+    _need(vols, "torch.float32", B * plan.N ** 3, "vols")
+    if coeffs is None:
+        coeffs = torch.empty((B, plan.Nb, 2), dtype=torch.float32, device=vols.device)
+    _need(coeffs, "torch.float32", B * plan.Nb * 2, "coeffs")
+    _check(lib().bh_expand(plan.handle, _ptr(vols), B, _ptr(coeffs), _stream(stream)), "bh_expand")
+    return coeffs
+
+
+# ------------------------------------------------------------------ score and gradient
+def bh_score_grad(plan: Plan, tmpl, sub, quats, L: int, with_grad: bool = True, stream=None):
+    """tmpl (Nb,2), sub (B,Nb,2), quats (B,S,4) CUDA float32 -> score (B,S), grad (B,S,3) or None."""
+    import torch
+    B, S = quats.shape[0], quats.shape[1]
+    _need(tmpl, "torch.float32", plan.Nb * 2, "tmpl")
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    _need(quats, "torch.float32", B * S * 4, "quats")
+    score = torch.empty((B, S), dtype=torch.float32, device=sub.device)
+    grad = torch.empty((B, S, 3), dtype=torch.float32, device=sub.device) if with_grad else None
+    _check(lib().bh_score_grad(plan.handle, _ptr(tmpl), _ptr(sub), B, _ptr(quats), S, L, _ptr(score), _ptr(grad),
+                               _stream(stream)), "bh_score_grad")
+    return score, grad
+
+
+# ------------------------------------------------------------------ alignment
+def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
+                   n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None):
+    """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
+    import torch
+    B, S = starts.shape[0], starts.shape[1]
+    dev = sub.device
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    _need(starts, "torch.float32", B * S * 4, "starts")
+    _need(tmpl, "torch.float32", plan.Nb * 2 * max(1, n_templates), "tmpl")
+    quat = quat_out if quat_out is not None else torch.empty((B, 4), dtype=torch.float32, device=dev)
+    score = score_out if score_out is not None else torch.empty((B,), dtype=torch.float32, device=dev)
+    st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
+    o = AlignOpts()
+    o.group = group
+    sq = ss = None
+    if per_start:
+        sq = torch.empty((B, S, 4), dtype=torch.float32, device=dev)
+        ss = torch.empty((B, S), dtype=torch.float32, device=dev)
+        o.start_quat_out, o.start_score_out = _ptr(sq), _ptr(ss)
+    if tmpl_index is not None:
+        _need(tmpl_index, "torch.int32", B, "tmpl_index")
+        o.tmpl_index, o.n_templates = _ptr(tmpl_index), n_templates
+    _check(lib().bh_align_batch(plan.handle, _ptr(tmpl), _ptr(sub), B, _ptr(starts), S, st, len(stages), steps,
+                                _ptr(quat), _ptr(score), ctypes.byref(o), _stream(stream)), "bh_align_batch")
+    if per_start:
+        return quat, score, sq, ss
+    return quat, score

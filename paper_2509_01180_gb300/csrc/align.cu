@@ -1,0 +1,446 @@
+// Rotational cross-correlation of Eq. 2 at s = 0, its closed-form gradient, and the multi-start
+// gradient ascent with frequency marching of Sec. II-C, for many subtomograms in one launch.
+//
+// Score of a rotation R (quaternion q):  S(R) = Re sum_{l<=L} sum_{m,n} xi^l_{mn} D^l_{mn}(R),
+// xi^l_{mn} = sum_k conj(t_klm) f_kln.  With R = Rz(alpha) Ry(beta) Rz(gamma),
+// D^l_{mn} = e^{-i m alpha} d^l_{mn}(beta) e^{-i n gamma}, so
+//   S = sum_{m,n} Re( e^{-i(m alpha + n gamma)} sum_{l >= max|m|,|n|} d^l_{mn}(beta) xi^l_{mn} ).
+// Each (m,n) pair is one l-recursion; the GPU never forms D.
+//
+// Folding (real volumes, so xi^l_{-m,-n} = (-1)^{m+n} conj(xi^l_{mn})), and d^l_{nm} = (-1)^{m-n} d^l_{mn}:
+// the four pairs (m,n), (n,m), (-m,-n), (-n,-m) share one recursion, and (-m,-n) contributes what
+// (m,n) contributes.  An "orbit" (m,n) with m >= |n| therefore carries two slots (m,n) and (n,m) with
+// weights 2 (1 for (0,0), slot (n,m) dropped on the diagonals n = +-m).  Its entries for l = m..Lb
+// are stored contiguously in shared memory as float4 (w1 xi_mn, w2 (-1)^{m-n} xi_nm).
+//
+// d^l_{mn}(beta) for l >= m >= |n| by the three-term recursion in l,
+//   d^l = A_l (cos beta - B_l) d^{l-1} - C_l d^{l-2},
+//   A_l = l(2l-1)/u_l, B_l = m n /(l(l-1)), C_l = l u_{l-1} / ((l-1) u_l), u_l = sqrt((l^2-m^2)(l^2-n^2)),
+// started from the closed form d^m_{mn} = (-1)^{m-n} sqrt(C(2m, m+n)) cos(beta/2)^{m+n} sin(beta/2)^{m-n},
+// and its beta-derivative by differentiating the same recursion.  The Euler angles never appear
+// explicitly: cos(beta/2) = |(w,z)|, sin(beta/2) = |(x,y)|, e^{i(alpha+gamma)/2} = (w + i z)/cos(beta/2),
+// e^{i(alpha-gamma)/2} = (y - i x)/sin(beta/2).
+//
+// Gradient along right perturbations R exp(eps J_i) (body axes): from dS/dalpha, dS/dbeta, dS/dgamma
+// with the ZYZ body angular velocity  omega = alpha'(-sb cg, sb sg, cb) + beta'(sg, cg, 0) + gamma'(0,0,1):
+//   g_z = dS/dgamma,  g_x sg + g_y cg = dS/dbeta,  g_x cg - g_y sg = (cos beta dS/dgamma - dS/dalpha)/sin beta.
+// (At sin beta -> 0 the last line loses FP32 precision as eps/|sin beta|; exactly at 0 it is taken as 0.)
+//
+// Work split: one CTA per subtomogram; lane group of G threads per start; within a row m the 2m+1
+// orbits are dealt round-robin to the G lanes, which reduce their partial sums by xor-shuffles.
+#include <cmath>
+#include <mutex>
+
+#include "bh_internal.h"
+
+namespace bh {
+namespace {
+
+constexpr int kBinStride = 2 * kMaxL + 1;
+__constant__ float4 c_lconst[kMaxL + 2];                   // (l(2l-1), (2l-1)/(l-1), l/(l-1), 0)
+__constant__ float c_lbin[(kMaxL + 1) * kBinStride];       // 0.5 log2 C(2m, m+n) at [m][m+n]
+
+constexpr int kMaxStages = 8;
+constexpr int kMaxThreads = 512;  // threads per CTA (S * G rounded up to a warp)
+
+struct AlignArgs {
+  Layout lay;
+  const float2* tmpl;
+  const int* tmpl_index;
+  int n_templates;
+  const float2* sub;
+  int B;
+  const float4* starts;  // [B][S] rotations (align) or evaluation rotations (score)
+  int S;
+  int nstages;
+  int stages[kMaxStages];
+  int steps;
+  int Lb;  // band of the shared-memory table
+  float4* quat_out;
+  float* score_out;
+  float4* start_quat_out;
+  float* start_score_out;
+  float* grad_out;  // score kernel: [B][S][3]
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cpow(float2 a, int k) {
+  float2 r = make_float2(1.f, 0.f);
+  for (int i = 0; i < k; ++i) r = cmul(r, a);
+  return r;
+}
+
+// Entries before row m of an orbit table of band Lb: sum_{j<m} (2j+1)(Lb-j+1).
+__host__ __device__ __forceinline__ int tab_base(int m, int Lb) {
+  return (Lb + 1) * m * m - ((m - 1) * m * (2 * m - 1) / 3 + (m - 1) * m / 2);
+}
+
+__device__ __forceinline__ float4 qnormalize(float4 q) {
+  const float r = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  return make_float4(q.x * r, q.y * r, q.z * r, q.w * r);
+}
+
+// Hamilton product a*b of quaternions stored (w, x, y, z) in (x, y, z, w) of a float4.
+__device__ __forceinline__ float4 qmul(float4 a, float4 b) {
+  return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w, a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                     a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y, a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+
+// Orbit table of one subtomogram (see header comment) for l <= Lb.
+__device__ void build_table(float4* __restrict__ tab, const Layout& lay, const float2* __restrict__ tmpl,
+                            const float2* __restrict__ sub, int Lb, int tid, int nth) {
+  const int nent = tab_base(Lb + 1, Lb);
+  for (int e = tid; e < nent; e += nth) {
+    int m = 0;
+    while (tab_base(m + 1, Lb) <= e) ++m;
+    const int len = Lb - m + 1;
+    const int rem = e - tab_base(m, Lb);
+    const int n = rem / len - m, l = m + rem % len;
+    const int K = lay.K[l], off = lay.off[l], w = 2 * l + 1;
+    const bool two = (m > 0) && (n != m) && (n != -m);
+    float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+      const float2 tm = __ldg(tmpl + off + k * w + m + l), fn = __ldg(sub + off + k * w + n + l);
+      x1.x += tm.x * fn.x + tm.y * fn.y;
+      x1.y += tm.x * fn.y - tm.y * fn.x;
+      if (two) {
+        const float2 tn = __ldg(tmpl + off + k * w + n + l), fm = __ldg(sub + off + k * w + m + l);
+        x2.x += tn.x * fm.x + tn.y * fm.y;
+        x2.y += tn.x * fm.y - tn.y * fm.x;
+      }
+    }
+    const float w1 = (m == 0) ? 1.f : 2.f;
+    const float w2 = two ? (((m - n) & 1) ? -2.f : 2.f) : 0.f;
+    tab[e] = make_float4(w1 * x1.x, w1 * x1.y, w2 * x2.x, w2 * x2.y);
+  }
+}
+
+struct Eval {
+  float S, gx, gy, gz;
+};
+
+// Score and body-frame gradient of rotation q at band L (FP32), from the orbit table of band Lb >= L.
+// Every lane of a G-group returns the same (bitwise) result.
+template <int G>
+__device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg) {
+  const float w = q.x, x = q.y, y = q.z, z = q.w;
+  const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+  const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);   // e^{i(alpha+gamma)/2}
+  const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);  // e^{i(alpha-gamma)/2}
+  const float xb = (cb - sb) * (cb + sb);                                             // cos beta
+  const float sinb = 2.f * cb * sb;                                                   // sin beta
+  const float lc = cb > 0.f ? fmaxf(log2f(cb), -500.f) : -500.f;
+  const float ls = sb > 0.f ? fmaxf(log2f(sb), -500.f) : -500.f;
+  const float2 Es = cconj(es);
+  const float2 EsG = cpow(Es, G), edG = cpow(ed, G);
+  const float2 Ed = cconj(ed);
+  const float2 Ed2 = cmul(Ed, Ed);
+  const float2 Uq = cpow(Es, qg);
+  float2 Wrow = cpow(ed, qg);
+  float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
+  for (int m = 0; m <= L; ++m) {
+    const int len = Lb - m + 1;
+    const float4* rowp = tab + tab_base(m, Lb);
+    float2 U = Uq, W = Wrow;
+    for (int n = qg - m; n <= m; n += G) {
+      const float4* e = rowp + (n + m) * len;
+      const float lb = c_lbin[m * kBinStride + m + n];
+      const float sg = ((m - n) & 1) ? -1.f : 1.f;
+      const float fa = (float)(m + n), fd = (float)(m - n);
+      const float d = sg * exp2f(lb + fa * lc + fd * ls);
+      float dp = 0.f;
+      if (m != n) dp += 0.5f * fd * exp2f(lb + (fa + 1.f) * lc + (fd - 1.f) * ls);
+      if (m + n != 0) dp -= 0.5f * fa * exp2f(lb + (fa - 1.f) * lc + (fd + 1.f) * ls);
+      dp *= sg;
+      float4 xv = e[0];
+      float a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
+      float b1r = dp * xv.x, b1i = dp * xv.y, b2r = dp * xv.z, b2i = dp * xv.w;
+      float d1 = d, d2 = 0.f, p1 = dp, p2 = 0.f, uprev = 0.f;
+      const float fm2 = (float)(m * m), fn2 = (float)(n * n), fmn = (float)(m * n);
+      for (int l = m + 1; l <= L; ++l) {
+        const float fl2 = (float)(l * l);
+        const float pp = (fl2 - fm2) * (fl2 - fn2);
+        const float iu = rsqrtf(pp);
+        const float4 k = c_lconst[l];
+        const float A = k.x * iu, AB = k.y * fmn * iu, Cc = k.z * uprev * iu;
+        uprev = pp * iu;
+        const float t = fmaf(A, xb, -AB);
+        const float dn = fmaf(t, d1, -Cc * d2);
+        const float pn = fmaf(t, p1, fmaf(-Cc, p2, -A * sinb * d1));
+        d2 = d1;
+        d1 = dn;
+        p2 = p1;
+        p1 = pn;
+        xv = e[l - m];
+        a1r = fmaf(dn, xv.x, a1r);
+        a1i = fmaf(dn, xv.y, a1i);
+        a2r = fmaf(dn, xv.z, a2r);
+        a2i = fmaf(dn, xv.w, a2i);
+        b1r = fmaf(pn, xv.x, b1r);
+        b1i = fmaf(pn, xv.y, b1i);
+        b2r = fmaf(pn, xv.z, b2r);
+        b2i = fmaf(pn, xv.w, b2i);
+      }
+      const float2 P1 = cmul(U, W), P2 = cmul(U, cconj(W));
+      const float2 z1 = cmul(P1, make_float2(a1r, a1i)), z2 = cmul(P2, make_float2(a2r, a2i));
+      S += z1.x + z2.x;
+      Sa += (float)m * z1.y + (float)n * z2.y;
+      Sg += (float)n * z1.y + (float)m * z2.y;
+      Sb += (P1.x * b1r - P1.y * b1i) + (P2.x * b2r - P2.y * b2i);
+      U = cmul(U, EsG);
+      W = cmul(W, edG);
+    }
+    Wrow = cmul(Wrow, Ed2);
+  }
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    S += __shfl_xor_sync(0xffffffffu, S, o);
+    Sa += __shfl_xor_sync(0xffffffffu, Sa, o);
+    Sb += __shfl_xor_sync(0xffffffffu, Sb, o);
+    Sg += __shfl_xor_sync(0xffffffffu, Sg, o);
+  }
+  const float2 eg = cmul(es, cconj(ed));  // e^{i gamma}
+  const float Q = (sinb > 1e-30f) ? (xb * Sg - Sa) / sinb : 0.f;
+  Eval r;
+  r.S = S;
+  r.gx = Sb * eg.y + Q * eg.x;
+  r.gy = Sb * eg.x - Q * eg.y;
+  r.gz = Sg;
+  return r;
+}
+
+__device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p) {
+  if (!a.tmpl_index) return a.tmpl;
+  int t = a.tmpl_index[p];
+  t = t < 0 ? 0 : (t >= a.n_templates ? a.n_templates - 1 : t);
+  return a.tmpl + (size_t)t * a.lay.Nb;
+}
+
+// Multi-start marching ascent; one CTA per subtomogram, blockDim = roundup(S*G, 32).
+template <int G>
+__global__ void __launch_bounds__(512) k_align(const AlignArgs a) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  const int s = threadIdx.x / G, qg = threadIdx.x % G;
+  const bool active = s < a.S;
+  const int se = active ? s : s % a.S;  // lanes past the last start shadow a real one and write nothing
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.Lb, threadIdx.x, blockDim.x);
+  __syncthreads();
+
+  float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
+  Eval cur;
+  cur.S = 0.f;
+  cur.gx = cur.gy = cur.gz = 0.f;
+  for (int st = 0; st < a.nstages; ++st) {
+    const int L = a.stages[st];
+    const float hmax = 3.14159265358979f / (float)L;
+    float h = 0.5f * hmax;
+    cur = eval_rotation<G>(smem_tab, a.Lb, L, q, qg);
+    for (int t = 0; t < a.steps; ++t) {
+      const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
+      const bool stop = !(gn > 1e-12f * fabsf(cur.S));
+      const float inv = stop ? 0.f : 1.f / gn;
+      float sh, ch;
+      sincosf(stop ? 0.f : 0.5f * h, &sh, &ch);
+      const float4 dq = make_float4(ch, sh * cur.gx * inv, sh * cur.gy * inv, sh * cur.gz * inv);
+      const float4 qt = qnormalize(qmul(q, dq));
+      const Eval tr = eval_rotation<G>(smem_tab, a.Lb, L, qt, qg);
+      if (!stop) {
+        if (tr.S > cur.S) {
+          q = qt;
+          cur = tr;
+          h = fminf(1.5f * h, hmax);
+        } else {
+          h *= 0.5f;
+        }
+      }
+    }
+  }
+  __syncthreads();  // the table is no longer read: reuse shared memory for the selection
+  float* sS = reinterpret_cast<float*>(smem_tab);
+  float4* sQ = reinterpret_cast<float4*>(sS + ((a.S + 3) & ~3));
+  if (active && qg == 0) {
+    sS[s] = cur.S;
+    sQ[s] = q;
+    if (a.start_quat_out) a.start_quat_out[(size_t)p * a.S + s] = q;
+    if (a.start_score_out) a.start_score_out[(size_t)p * a.S + s] = cur.S;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int j = 1; j < a.S; ++j)
+      if (sS[j] > sS[best]) best = j;
+    a.quat_out[p] = sQ[best];
+    a.score_out[p] = sS[best];
+  }
+}
+
+// Score and gradient at given rotations; one CTA per subtomogram.
+template <int G>
+__global__ void __launch_bounds__(512) k_score(const AlignArgs a, int L) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  const int s = threadIdx.x / G, qg = threadIdx.x % G;
+  const bool active = s < a.S;
+  const int se = active ? s : s % a.S;
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.Lb, threadIdx.x, blockDim.x);
+  __syncthreads();
+  const float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
+  const Eval r = eval_rotation<G>(smem_tab, a.Lb, L, q, qg);
+  if (active && qg == 0) {
+    a.score_out[(size_t)p * a.S + s] = r.S;
+    if (a.grad_out) {
+      float* g = a.grad_out + ((size_t)p * a.S + s) * 3;
+      g[0] = r.gx;
+      g[1] = r.gy;
+      g[2] = r.gz;
+    }
+  }
+}
+
+size_t table_bytes(int Lb) { return (size_t)tab_base(Lb + 1, Lb) * sizeof(float4); }
+
+template <int G>
+int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stream) {
+  const int threads = round_up(a.S * G, 32);
+  const size_t sel = (size_t)((a.S + 3) & ~3) * sizeof(float) + (size_t)a.S * sizeof(float4);
+  const size_t smem = std::max(table_bytes(a.Lb), score_only ? (size_t)16 : sel);
+  if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
+  if (score_only) {
+    BH_CUDA_TRY(cudaFuncSetAttribute(k_score<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_score<G><<<a.B, threads, smem, stream>>>(a, L);
+  } else {
+    BH_CUDA_TRY(cudaFuncSetAttribute(k_align<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_align<G><<<a.B, threads, smem, stream>>>(a);
+  }
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t stream) {
+  switch (G) {
+    case 1: return launch_align_g<1>(a, score_only, L, stream);
+    case 2: return launch_align_g<2>(a, score_only, L, stream);
+    case 4: return launch_align_g<4>(a, score_only, L, stream);
+    case 8: return launch_align_g<8>(a, score_only, L, stream);
+    case 16: return launch_align_g<16>(a, score_only, L, stream);
+    default: return fail(BH_ERR_ARG, "group %d not in {1,2,4,8,16}", G);
+  }
+}
+
+// Default lanes per start: aim at >= 128 threads per CTA, capped by 1024 threads and 16 lanes.
+int default_group(int S) {
+  int G = 1;
+  while (G < 16 && S * G < 128 && S * G * 2 <= kMaxThreads) G *= 2;
+  return G;
+}
+
+}  // namespace
+
+int align_init_constants() {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  BH_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev < 128 && done[dev]) return BH_OK;
+  float4 lc[kMaxL + 2];
+  for (int l = 0; l < kMaxL + 2; ++l) {
+    if (l < 2) {
+      lc[l] = make_float4((float)(l * (2 * l - 1)), 0.f, 0.f, 0.f);
+    } else {
+      lc[l] = make_float4((float)(l * (2 * l - 1)), (float)((2.0 * l - 1.0) / (l - 1.0)), (float)((double)l / (l - 1.0)),
+                          0.f);
+    }
+  }
+  static float lb[(kMaxL + 1) * kBinStride];
+  for (int m = 0; m <= kMaxL; ++m)
+    for (int j = 0; j <= 2 * m; ++j)
+      lb[m * kBinStride + j] =
+          (float)(0.5 * (std::lgamma(2.0 * m + 1.0) - std::lgamma(j + 1.0) - std::lgamma(2.0 * m - j + 1.0)) / std::log(2.0));
+  BH_CUDA_TRY(cudaMemcpyToSymbol(c_lconst, lc, sizeof(lc)));
+  BH_CUDA_TRY(cudaMemcpyToSymbol(c_lbin, lb, sizeof(lb)));
+  if (dev < 128) done[dev] = true;
+  return BH_OK;
+}
+
+}  // namespace bh
+
+using namespace bh;
+
+static int check_common(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* quats, int S) {
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
+  if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d outside 1..%d", S, kMaxThreads);
+  if (B > 0 && (!tmpl || !sub || !quats)) return fail(BH_ERR_ARG, "NULL input array");
+  return BH_OK;
+}
+
+extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* quats, int S,
+                             int L, float* score, float* grad, void* stream) {
+  clear_error();
+  int st = check_common(p, tmpl, sub, B, quats, S);
+  if (st != BH_OK) return st;
+  if (L < 0 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 0..%d", L, p->Lmax);
+  if (B == 0) return BH_OK;
+  if (!score) return fail(BH_ERR_ARG, "score is NULL");
+  AlignArgs a{};
+  a.lay = p->layout;
+  a.tmpl = reinterpret_cast<const float2*>(tmpl);
+  a.sub = reinterpret_cast<const float2*>(sub);
+  a.B = B;
+  a.starts = reinterpret_cast<const float4*>(quats);
+  a.S = S;
+  a.Lb = L;
+  a.score_out = score;
+  a.grad_out = grad;
+  int G = default_group(S);
+  return launch_align(a, G, true, L, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* starts, int S,
+                              const int* stages, int nstages, int steps, float* quat_out, float* score_out,
+                              const bh_align_opts* opts, void* stream) {
+  clear_error();
+  int st = check_common(p, tmpl, sub, B, starts, S);
+  if (st != BH_OK) return st;
+  if (!stages || nstages < 1 || nstages > kMaxStages) return fail(BH_ERR_ARG, "nstages=%d outside 1..%d", nstages, kMaxStages);
+  for (int i = 0; i < nstages; ++i) {
+    if (stages[i] < 1 || stages[i] > p->Lmax) return fail(BH_ERR_ARG, "stage band %d outside 1..%d", stages[i], p->Lmax);
+    if (i > 0 && stages[i] <= stages[i - 1]) return fail(BH_ERR_ARG, "stage bands must increase");
+  }
+  if (steps < 0 || steps > 100000) return fail(BH_ERR_ARG, "steps=%d outside 0..100000", steps);
+  if (B == 0) return BH_OK;
+  if (!quat_out || !score_out) return fail(BH_ERR_ARG, "quat_out or score_out is NULL");
+  AlignArgs a{};
+  a.lay = p->layout;
+  a.tmpl = reinterpret_cast<const float2*>(tmpl);
+  a.sub = reinterpret_cast<const float2*>(sub);
+  a.B = B;
+  a.starts = reinterpret_cast<const float4*>(starts);
+  a.S = S;
+  a.nstages = nstages;
+  for (int i = 0; i < nstages; ++i) a.stages[i] = stages[i];
+  a.steps = steps;
+  a.Lb = stages[nstages - 1];
+  a.quat_out = reinterpret_cast<float4*>(quat_out);
+  a.score_out = score_out;
+  int G = 0;
+  if (opts) {
+    if (opts->tmpl_index) {
+      if (opts->n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d with tmpl_index", opts->n_templates);
+      a.tmpl_index = opts->tmpl_index;
+      a.n_templates = opts->n_templates;
+    }
+    a.start_quat_out = reinterpret_cast<float4*>(opts->start_quat_out);
+    a.start_score_out = opts->start_score_out;
+    G = opts->group;
+    if (opts->refine_fp64) return fail(BH_ERR_UNSUPPORTED, "refine_fp64 is not available in this build");
+  }
+  if (G == 0) G = p->align_group[a.Lb] > 0 ? p->align_group[a.Lb] : default_group(S);
+  if (round_up(S * G, 32) > kMaxThreads) return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
+  return launch_align(a, G, false, 0, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,88 @@
+// Internal declarations shared by the libbh translation units (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bh.h"
+
+namespace bh {
+
+// Record a message for bh_last_error() and return `code`.
+int fail(int code, const char* fmt, ...);
+void clear_error();
+
+#define BH_CUDA_TRY(call)                                                                           \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess)                                                                          \
+      return ::bh::fail(e_ == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+  } while (0)
+
+#define BH_CHECK_LAUNCH()                                                                           \
+  do {                                                                                              \
+    cudaError_t e_ = cudaGetLastError();                                                            \
+    if (e_ != cudaSuccess)                                                                          \
+      return ::bh::fail(BH_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                  \
+  } while (0)
+
+constexpr int kMaxL = 64;
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+inline int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Coefficient layout passed by value to kernels: off[l] = first slot of degree l, K[l] = roots kept.
+struct Layout {
+  int Lmax;
+  int Nb;
+  int off[kMaxL + 2];
+  int K[kMaxL + 1];
+};
+
+// GEMM tiling of the tensor-core expansion.
+constexpr int kGemmBM = 128;
+constexpr int kGemmBK = 64;
+constexpr int kPadV = 64;    // V is padded to a multiple of the K block
+constexpr int kPadNb = 256;  // Nb is padded to a multiple of the widest N tile
+
+}  // namespace bh
+
+struct bh_plan {
+  int device = -1;
+  int N = 0, Lmax = 0, mode = 0, max_batch = 0;
+  double lam_max = 0;
+  int V = 0, V_pad = 0, Nb = 0, Nb_pad = 0, M_cap = 0;
+  std::vector<int> K, offs;         // per degree
+  std::vector<double> lam, cst;     // lambda_lk, c_lk flattened by degree
+  bh::Layout layout{};
+
+  int* d_vox = nullptr;             // [V] flat voxel index of each in-ball voxel
+  int2* d_slot = nullptr;           // [Nb] real-GEMM columns feeding each complex slot (signed, 1-based)
+  float* d_T32 = nullptr;           // [Nb_pad][V_pad] basis table, FP32 mode
+  __nv_bfloat16* d_Thi = nullptr;   // [Nb_pad][V_pad] BF16 hi part
+  __nv_bfloat16* d_Tlo = nullptr;   // [Nb_pad][V_pad] BF16 lo part
+  float* d_X32 = nullptr;           // [M_cap][V_pad] gathered volumes (FP32 mode)
+  __nv_bfloat16* d_Xhi = nullptr;   // [M_cap][V_pad] gathered volumes, hi part
+  __nv_bfloat16* d_Xlo = nullptr;   // [M_cap][V_pad] lo part
+  float* d_C = nullptr;             // [M_cap][Nb_pad] real GEMM output
+  int* d_err = nullptr;             // device status word written by bounded waits
+  int gemm_bn = 256;                // N tile of the tensor-core GEMM
+  CUtensorMap tm_xhi, tm_xlo, tm_thi, tm_tlo;  // TMA descriptors (BF16 mode)
+  int align_group[bh::kMaxL + 1];   // autotuned lanes-per-start by top band (0 = not tuned)
+};
+
+namespace bh {
+// expand.cu
+int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const std::vector<double>& angular,
+                 const std::vector<int>& vox_r2, const std::vector<int2>& colinfo, double h3);
+int make_tensor_maps(bh_plan* p);
+// align.cu
+int align_init_constants();
+}  // namespace bh

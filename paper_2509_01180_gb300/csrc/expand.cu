@@ -1,0 +1,500 @@
+// Expansion of voxel volumes into ball-harmonic coefficients (Sec. II-A, expansion display) as a dense
+// voxel-by-basis contraction:  C[b][j] = sum_v X[b][v] T[j][v],  X = in-ball voxels of volume b,
+// T = real-form basis table (one row per coefficient slot, h^3 folded in; see plan.cpp).
+//
+// Two arithmetic forms:
+//   BH_MODE_FP32        plain FP32 FFMA GEMM (128x128 tiles, 8x8 per thread).
+//   BH_MODE_BF16_SPLIT  5th-generation tensor cores: tcgen05.mma kind::f16 with BF16 operands staged by
+//                       TMA (128-byte swizzle) through an mbarrier pipeline and an FP32 accumulator in
+//                       TMEM.  X = Xh + Xl and T = Th + Tl are split into BF16 hi/lo parts and the three
+//                       products Xh*Th + Xh*Tl + Xl*Th accumulate into the same tile (the Xl*Tl term,
+//                       ~2^-16 relative, is dropped).
+// The real GEMM columns are then combined into complex coefficients [b][l][k][m+l].
+#include <cstdio>
+
+#include "bh_internal.h"
+
+namespace bh {
+namespace {
+
+// ---------------------------------------------------------------- basis table (FP64 -> storage form)
+__global__ void k_build_table(const double* __restrict__ radial, int n_r2, const double* __restrict__ angular,
+                              const int* __restrict__ vox_r2, const int2* __restrict__ colinfo, double h3, int V,
+                              int V_pad, int Nb, float* __restrict__ T32, __nv_bfloat16* __restrict__ Thi,
+                              __nv_bfloat16* __restrict__ Tlo) {
+  const int j = blockIdx.y;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V_pad) return;
+  double val = 0.0;
+  if (j < Nb && v < V) {
+    const int2 ci = colinfo[j];
+    val = h3 * radial[(size_t)ci.x * n_r2 + vox_r2[v]] * angular[(size_t)ci.y * V + v];
+  }
+  const size_t o = (size_t)j * V_pad + v;
+  if (T32) T32[o] = (float)val;
+  if (Thi) {
+    const __nv_bfloat16 hi = __double2bfloat16(val);
+    Thi[o] = hi;
+    Tlo[o] = __double2bfloat16(val - (double)__bfloat162float(hi));
+  }
+}
+
+// ---------------------------------------------------------------- gather in-ball voxels (+ hi/lo split)
+__global__ void k_gather(const float* __restrict__ vols, int B, long long N3, const int* __restrict__ vox, int V,
+                         int V_pad, float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
+                         __nv_bfloat16* __restrict__ Xlo) {
+  const int b = blockIdx.y;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V_pad) return;
+  const float x = (b < B && v < V) ? __ldg(vols + (size_t)b * N3 + vox[v]) : 0.0f;
+  const size_t o = (size_t)b * V_pad + v;
+  if (X32) X32[o] = x;
+  if (Xhi) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    Xhi[o] = hi;
+    Xlo[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
+  }
+}
+
+// ---------------------------------------------------------------- real columns -> complex coefficients
+// slot[s] = (re source, im source), 1-based column index with sign, 0 = zero.
+__global__ void k_to_complex(const float* __restrict__ C, int ldc, int B, int Nb, const int2* __restrict__ slot,
+                             float2* __restrict__ out) {
+  const int b = blockIdx.y;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || s >= Nb) return;
+  const int2 src = slot[s];
+  const float* row = C + (size_t)b * ldc;
+  float re = 0.f, im = 0.f;
+  if (src.x > 0) re = row[src.x - 1]; else if (src.x < 0) re = -row[-src.x - 1];
+  if (src.y > 0) im = row[src.y - 1]; else if (src.y < 0) im = -row[-src.y - 1];
+  out[(size_t)b * Nb + s] = make_float2(re, im);
+}
+
+// ---------------------------------------------------------------- plain FP32 GEMM, both operands K-major
+// C[M][N] = A[M][K] * B[N][K]^T; M % 128 == 0, N % 128 == 0, K % 16 == 0.
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16, SG_PAD = 4;
+
+__global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, const float* __restrict__ Bm,
+                                                  float* __restrict__ C, int M, int N, int K) {
+  __shared__ __align__(16) float As[SG_BK][SG_BM + SG_PAD];
+  __shared__ __align__(16) float Bs[SG_BK][SG_BN + SG_PAD];
+  const int tid = threadIdx.x;
+  const int m0 = blockIdx.y * SG_BM, n0 = blockIdx.x * SG_BN;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: rows lr and lr+64, k columns lk..lk+3
+  const int tx = tid & 15, ty = tid >> 4;
+  const float* Ap0 = A + (size_t)(m0 + lr) * K + lk;
+  const float* Ap1 = Ap0 + (size_t)64 * K;
+  const float* Bp0 = Bm + (size_t)(n0 + lr) * K + lk;
+  const float* Bp1 = Bp0 + (size_t)64 * K;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float4 a0 = __ldg(reinterpret_cast<const float4*>(Ap0)), a1 = __ldg(reinterpret_cast<const float4*>(Ap1));
+  float4 b0 = __ldg(reinterpret_cast<const float4*>(Bp0)), b1 = __ldg(reinterpret_cast<const float4*>(Bp1));
+  for (int k0 = 0; k0 < K; k0 += SG_BK) {
+    __syncthreads();
+    As[lk + 0][lr] = a0.x; As[lk + 1][lr] = a0.y; As[lk + 2][lr] = a0.z; As[lk + 3][lr] = a0.w;
+    As[lk + 0][lr + 64] = a1.x; As[lk + 1][lr + 64] = a1.y; As[lk + 2][lr + 64] = a1.z; As[lk + 3][lr + 64] = a1.w;
+    Bs[lk + 0][lr] = b0.x; Bs[lk + 1][lr] = b0.y; Bs[lk + 2][lr] = b0.z; Bs[lk + 3][lr] = b0.w;
+    Bs[lk + 0][lr + 64] = b1.x; Bs[lk + 1][lr + 64] = b1.y; Bs[lk + 2][lr + 64] = b1.z; Bs[lk + 3][lr + 64] = b1.w;
+    __syncthreads();
+    if (k0 + SG_BK < K) {  // prefetch the next K block into registers while computing this one
+      a0 = __ldg(reinterpret_cast<const float4*>(Ap0 + k0 + SG_BK));
+      a1 = __ldg(reinterpret_cast<const float4*>(Ap1 + k0 + SG_BK));
+      b0 = __ldg(reinterpret_cast<const float4*>(Bp0 + k0 + SG_BK));
+      b1 = __ldg(reinterpret_cast<const float4*>(Bp1 + k0 + SG_BK));
+    }
+#pragma unroll
+    for (int kk = 0; kk < SG_BK; ++kk) {
+      const float4 ra0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 ra1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+      const float4 rb0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float4 rb1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+      const float ra[8] = {ra0.x, ra0.y, ra0.z, ra0.w, ra1.x, ra1.y, ra1.z, ra1.w};
+      const float rb[8] = {rb0.x, rb0.y, rb0.z, rb0.w, rb1.x, rb1.y, rb1.z, rb1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ra[i], rb[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    float* crow = C + (size_t)row * N + n0;
+    *reinterpret_cast<float4*>(crow + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(crow + 64 + tx * 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+  }
+}
+
+// ---------------------------------------------------------------- tcgen05 / TMA / mbarrier primitives
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s of device time, records `code` in *err.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 0u && globaltimer_ns() - t0 > kWaitLimitNs) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte rows and the 128-byte swizzle:
+// start address >> 4 at bits [0,14), leading byte offset (unused for this layout) = 16 B at [16,30),
+// stride byte offset = 1024 B (one 8-row swizzle atom) at [32,46), descriptor version 1 at [46,48),
+// layout SWIZZLE_128B = 2 at [61,64).  Tiles are 1024-byte aligned, so the base offset is 0.
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits [4,6) = 1), A = B = BF16 (bits [7,10) and [10,13) = 1),
+// both K-major (bits 15, 16 = 0), N >> 3 at [17,23), M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int BN>
+struct TcCfg {
+  static constexpr int BM = kGemmBM, BK = kGemmBK;
+  static constexpr int STAGES = (BN >= 256) ? 2 : 3;
+  static constexpr uint32_t A_BYTES = BM * BK * 2;
+  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;  // + alignment slack
+};
+
+// One 128 x BN output tile per CTA of 4 warps.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs,
+// all four warps read the accumulator (warp w owns TMEM lanes 32w..32w+31 = tile rows) and store it.
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+              float* __restrict__ C, int ldc, int num_kb, int* __restrict__ err) {
+  using Cfg = TcCfg<BN>;
+  constexpr int ST = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * Cfg::BM, n0 = blockIdx.x * BN;
+  auto sA_hi = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES; };
+  auto sA_lo = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
+  auto sB_hi = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES; };
+  auto sB_lo = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES + Cfg::B_BYTES; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    mbar_fence_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base_sh, BN);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tacc = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int kb = 0;
+    for (; kb < num_kb; ++kb) {
+      const int s = kb % ST;
+      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, err, 101)) break;
+      mbar_arrive_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
+      const int kx = kb * Cfg::BK;
+      tma_load_2d(sA_hi(s), &tmAh, kx, m0, &full_bar[s]);
+      tma_load_2d(sA_lo(s), &tmAl, kx, m0, &full_bar[s]);
+      tma_load_2d(sB_hi(s), &tmBh, kx, n0, &full_bar[s]);
+      tma_load_2d(sB_lo(s), &tmBl, kx, n0, &full_bar[s]);
+    }
+    if (kb < num_kb) {
+      // gave up: let the copies already issued land before the CTA leaves (bounded again)
+      for (int j = (kb >= ST ? kb - ST : 0); j < kb; ++j) mbar_wait(&full_bar[j % ST], (uint32_t)(j / ST) & 1u, err, 102);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16_f32(Cfg::BM, BN);
+    for (int kb = 0; kb < num_kb; ++kb) {
+      const int s = kb % ST;
+      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, err, 103)) break;
+      tc_fence_after();
+      const uint64_t ah = sdesc_k_sw128(smem_u32(sA_hi(s))), al = sdesc_k_sw128(smem_u32(sA_lo(s)));
+      const uint64_t bh = sdesc_k_sw128(smem_u32(sB_hi(s))), bl = sdesc_k_sw128(smem_u32(sB_lo(s)));
+#pragma unroll
+      for (int k = 0; k < Cfg::BK / 16; ++k) {
+        const uint64_t adv = (uint64_t)(k * 32) >> 4;  // 16 BF16 = 32 bytes along K inside the swizzle atom
+        umma_bf16(tacc, ah + adv, bh + adv, idesc, (kb | k) != 0 ? 1u : 0u);
+        umma_bf16(tacc, ah + adv, bl + adv, idesc, 1u);
+        umma_bf16(tacc, al + adv, bh + adv, idesc, 1u);
+      }
+      umma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+    }
+    umma_commit(&done_bar);  // accumulator complete (also on the error path: waits for issued MMAs)
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: TMEM -> registers -> global
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0, err, 104));  // warp-uniform before tcgen05.ld
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  float* crow = C + (size_t)row * ldc + n0;
+#pragma unroll 1
+  for (int c = 0; c < BN / 32; ++c) {
+    uint32_t r[32];
+    tmem_ld_32x32b_x32(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+    tmem_ld_wait();
+    if (ok) {
+      float4* dst = reinterpret_cast<float4*>(crow + c * 32);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        dst[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]), __uint_as_float(r[4 * i + 2]),
+                             __uint_as_float(r[4 * i + 3]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tacc, BN);
+}
+
+}  // namespace
+
+// ====================================================================== host helpers
+int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const std::vector<double>& angular,
+                 const std::vector<int>& vox_r2, const std::vector<int2>& colinfo, double h3) {
+  double *d_rad = nullptr, *d_ang = nullptr;
+  int* d_r2 = nullptr;
+  int2* d_ci = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_rad);
+    cudaFree(d_ang);
+    cudaFree(d_r2);
+    cudaFree(d_ci);
+  };
+#define UT_TRY(call)                                                                                           \
+  do {                                                                                                         \
+    cudaError_t e_ = (call);                                                                                   \
+    if (e_ != cudaSuccess) {                                                                                   \
+      cleanup();                                                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    }                                                                                                          \
+  } while (0)
+  UT_TRY(cudaMalloc(&d_rad, sizeof(double) * radial.size()));
+  UT_TRY(cudaMalloc(&d_ang, sizeof(double) * angular.size()));
+  UT_TRY(cudaMalloc(&d_r2, sizeof(int) * vox_r2.size()));
+  UT_TRY(cudaMalloc(&d_ci, sizeof(int2) * colinfo.size()));
+  UT_TRY(cudaMemcpy(d_rad, radial.data(), sizeof(double) * radial.size(), cudaMemcpyHostToDevice));
+  UT_TRY(cudaMemcpy(d_ang, angular.data(), sizeof(double) * angular.size(), cudaMemcpyHostToDevice));
+  UT_TRY(cudaMemcpy(d_r2, vox_r2.data(), sizeof(int) * vox_r2.size(), cudaMemcpyHostToDevice));
+  UT_TRY(cudaMemcpy(d_ci, colinfo.data(), sizeof(int2) * colinfo.size(), cudaMemcpyHostToDevice));
+  dim3 grid((p->V_pad + 255) / 256, p->Nb_pad);
+  k_build_table<<<grid, 256>>>(d_rad, n_r2, d_ang, d_r2, d_ci, h3, p->V, p->V_pad, p->Nb, p->d_T32, p->d_Thi,
+                               p->d_Tlo);
+  UT_TRY(cudaGetLastError());
+  UT_TRY(cudaDeviceSynchronize());
+#undef UT_TRY
+  cleanup();
+  return BH_OK;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+static int encode_bf16_2d(CUtensorMap* tm, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                          uint32_t box_outer) {
+  auto enc = get_encode();
+  if (!enc) return fail(BH_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(BH_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return BH_OK;
+}
+
+int make_tensor_maps(bh_plan* p) {
+  // Operands are K-major: inner dimension = V_pad (multiple of 64), boxes 64 x rows.
+  int st;
+  if ((st = encode_bf16_2d(&p->tm_xhi, p->d_Xhi, p->V_pad, p->M_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_xlo, p->d_Xlo, p->V_pad, p->M_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_thi, p->d_Thi, p->V_pad, p->Nb_pad, kGemmBK, p->gemm_bn)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_tlo, p->d_Tlo, p->V_pad, p->Nb_pad, kGemmBK, p->gemm_bn)) != BH_OK) return st;
+  return BH_OK;
+}
+
+static int launch_gemm(bh_plan* p, int Mp, cudaStream_t stream) {
+  if (p->mode == BH_MODE_FP32) {
+    dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM);
+    k_sgemm_nt<<<grid, 256, 0, stream>>>(p->d_X32, p->d_T32, p->d_C, Mp, p->Nb_pad, p->V_pad);
+    BH_CHECK_LAUNCH();
+    return BH_OK;
+  }
+  const int num_kb = p->V_pad / kGemmBK;
+  if (p->gemm_bn == 256) {
+    static bool attr = false;
+    if (!attr) {
+      BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<256>::SMEM));
+      attr = true;
+    }
+    dim3 grid(p->Nb_pad / 256, Mp / kGemmBM);
+    k_gemm_tc<256><<<grid, 128, TcCfg<256>::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
+                                                            p->Nb_pad, num_kb, p->d_err);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TcCfg<128>::SMEM));
+      attr = true;
+    }
+    dim3 grid(p->Nb_pad / 128, Mp / kGemmBM);
+    k_gemm_tc<128><<<grid, 128, TcCfg<128>::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
+                                                            p->Nb_pad, num_kb, p->d_err);
+  }
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+}  // namespace bh
+
+using namespace bh;
+
+extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, void* stream_) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
+  if (B == 0) return BH_OK;
+  if (!vols || !coeffs) return fail(BH_ERR_ARG, "vols or coeffs is NULL");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const long long N3 = (long long)p->N * p->N * p->N;
+  for (int b0 = 0; b0 < B; b0 += p->max_batch) {
+    const int Bc = std::min(p->max_batch, B - b0);
+    const int Mp = round_up(Bc, kGemmBM);
+    dim3 g1((p->V_pad + 255) / 256, Mp);
+    k_gather<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, p->d_X32, p->d_Xhi,
+                                     p->d_Xlo);
+    BH_CHECK_LAUNCH();
+    int st = launch_gemm(p, Mp, stream);
+    if (st != BH_OK) return st;
+    dim3 g2((p->Nb + 255) / 256, Bc);
+    k_to_complex<<<g2, 256, 0, stream>>>(p->d_C, p->Nb_pad, Bc, p->Nb, p->d_slot,
+                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb);
+    BH_CHECK_LAUNCH();
+  }
+  return BH_OK;
+}

@@ -1,0 +1,248 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on identical seeded inputs.
+
+Tolerances (from the arithmetic; stated once here and in the design notes):
+  * coefficients: relative L2 error <= 1e-4 (FP32 GEMM: ~1e-7; BF16 hi/lo split: ~2^-16 per product)
+  * scores: |S_gpu - S_ref| <= 1e-4 * ||t_<=L|| ||f_<=L||  (the Cauchy-Schwarz bound of |S|)
+  * gradients: |g_gpu - g_ref| <= 1e-4 * (L+1) * ||t|| ||f|| away from sin(beta) ~ 0
+  * rotations: best rotation within 0.1 degree of the oracle's on identical starts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import align, ball, wigner  # noqa: E402
+from paper_2509_01180_gb300 import bh, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    bh.lib()
+    return torch.device("cuda:0")
+
+
+_plans = {}
+
+
+def plan_for(N, L, mode, max_batch=0):
+    key = (N, L, mode, max_batch)
+    if key not in _plans:
+        _plans[key] = bh.bh_plan_create(N, L, math.pi * N / 2, mode, max_batch)
+    return _plans[key]
+
+
+_bases = {}
+
+
+def basis_for(N, L):
+    if (N, L) not in _bases:
+        _bases[(N, L)] = ball.make_basis(L, math.pi * N / 2)
+    return _bases[(N, L)]
+
+
+def to_c(t):
+    a = t.detach().cpu().numpy().astype(np.float64)
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def to_f32(c):
+    return torch.from_numpy(np.stack([c.real, c.imag], -1).astype(np.float32))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------- expansion
+@pytest.mark.parametrize("mode", [bh.BH_MODE_FP32, bh.BH_MODE_BF16_SPLIT])
+@pytest.mark.parametrize("N,L,B,max_batch", [(16, 8, 5, 0), (16, 8, 130, 0), (16, 8, 37, 16), (32, 16, 9, 0)])
+def test_expand_matches_oracle(dev, mode, N, L, B, max_batch):
+    rng = np.random.default_rng(100 + N + B)
+    vols = rng.normal(size=(B, N, N, N)).astype(np.float32)
+    p = plan_for(N, L, mode, max_batch)
+    got = to_c(bh.bh_expand(p, torch.from_numpy(vols).to(dev)))
+    ref = ball.expand(basis_for(N, L), vols.astype(np.float64))
+    for b in range(B):
+        assert rel_l2(got[b], ref[b]) < 1e-4, (b, rel_l2(got[b], ref[b]))
+    if mode == bh.BH_MODE_FP32:
+        assert rel_l2(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("mode", [bh.BH_MODE_FP32, bh.BH_MODE_BF16_SPLIT])
+def test_expand_phantoms(dev, mode):
+    w = synth.make_workload("batch32", count=3)
+    p = plan_for(32, 16, mode)
+    got = to_c(bh.bh_expand(p, torch.from_numpy(w.vols).to(dev)))
+    ref = ball.expand(basis_for(32, 16), w.vols.astype(np.float64))
+    for b in range(3):
+        assert rel_l2(got[b], ref[b]) < 1e-4
+
+
+def test_expand_empty_batch_is_noop(dev):
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    out = torch.full((1, p.Nb, 2), 7.0, device=dev)
+    bh.lib().bh_expand(p.handle, 0, 0, out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert bool((out == 7.0).all())
+
+
+# ---------------------------------------------------------------------------- score and gradient
+def realish_coeffs(Bs, rng, n):
+    """Coefficients of real random volumes (conjugate-symmetric), computed by the oracle."""
+    N = 16
+    vols = rng.normal(size=(n, N, N, N))
+    return ball.expand(Bs, vols)
+
+
+def off_pole_quats(rng, n):
+    out = []
+    while len(out) < n:
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        sb = math.hypot(q[1], q[2])
+        cb = math.hypot(q[0], q[3])
+        if 2 * sb * cb > 0.05:
+            out.append(q)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 5, 8])
+def test_score_grad_matches_oracle(dev, L):
+    Bs = basis_for(16, 8)
+    rng = np.random.default_rng(7 + L)
+    c = realish_coeffs(Bs, rng, 4)
+    t, subs = c[0], c[1:]
+    B, S = 3, 7
+    quats = np.stack([off_pole_quats(rng, S) for _ in range(B)])
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    sc, gr = bh.bh_score_grad(p, to_f32(t).to(dev), to_f32(subs).to(dev),
+                              torch.from_numpy(quats.astype(np.float32)).to(dev), L)
+    sc, gr = sc.cpu().numpy(), gr.cpu().numpy()
+    o = Bs.offsets[L + 1]
+    for b in range(B):
+        xi = align.build_xi(Bs, t, subs[b], L)
+        scale = np.linalg.norm(t[:o]) * np.linalg.norm(subs[b][:o])
+        for s in range(S):
+            q = quats[b, s].astype(np.float32).astype(np.float64)
+            S_ref, g_ref = align.score_grad(xi, q, L)
+            assert abs(sc[b, s] - S_ref) <= 1e-4 * scale, (b, s, sc[b, s], S_ref)
+            assert np.max(np.abs(gr[b, s] - g_ref)) <= 1e-4 * (L + 1) * scale, (b, s, gr[b, s], g_ref)
+
+
+def test_score_at_identity_and_poles(dev):
+    """Rotations on the beta = 0 and beta = pi poles (Euler angles degenerate) still score correctly."""
+    Bs = basis_for(16, 8)
+    rng = np.random.default_rng(3)
+    c = realish_coeffs(Bs, rng, 2)
+    qs = np.array([[1, 0, 0, 0], [0, 0, 0, 1], [math.cos(0.3), 0, 0, math.sin(0.3)], [0, 1, 0, 0],
+                   [0, math.cos(0.7), math.sin(0.7), 0]], dtype=np.float64)
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    sc, _ = bh.bh_score_grad(p, to_f32(c[0]).to(dev), to_f32(c[1:2]).to(dev),
+                             torch.from_numpy(qs[None].astype(np.float32)).to(dev), 8)
+    xi = align.build_xi(Bs, c[0], c[1], 8)
+    scale = np.linalg.norm(c[0]) * np.linalg.norm(c[1])
+    for s, q in enumerate(qs):
+        assert abs(float(sc[0, s]) - align.score(xi, q, 8)) <= 1e-4 * scale
+
+
+# ---------------------------------------------------------------------------- alignment
+def oracle_align(w, b, Bs, t, f):
+    return align.align_particle(Bs, t, f, w.starts[b].astype(np.float64), w.stages, w.steps)
+
+
+def test_align_pair16_on_oracle_coefficients(dev):
+    """Plain method (16^3, l <= 8, 2-4-8, 8 starts, 50 steps): same coefficients and starts -> same optimum."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = oracle_align(w, 0, Bs, t, f)
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    q, s, sq, ss = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev),
+                                     torch.from_numpy(w.starts).to(dev), w.stages, w.steps, per_start=True)
+    q = q.cpu().numpy()[0].astype(np.float64)
+    assert math.degrees(wigner.geodesic_angle(q / np.linalg.norm(q), ref.q)) < 0.1
+    assert abs(float(s[0]) - ref.score) < 1e-4 * abs(ref.score)
+    # every start that converged to a clear maximum lands on the oracle's rotation for that start
+    sq = sq.cpu().numpy()[0].astype(np.float64)
+    agree = [math.degrees(wigner.geodesic_angle(sq[i] / np.linalg.norm(sq[i]), ref.start_q[i])) < 0.1
+             for i in range(w.S)]
+    assert sum(agree) >= w.S - 1
+
+
+@pytest.mark.parametrize("group", [1, 2, 4, 8, 16])
+def test_align_groups_agree(dev, group):
+    """The lane-group split of the orbit sums changes only rounding: every group size gives the oracle's optimum."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = oracle_align(w, 0, Bs, t, f)
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    q, _ = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev), torch.from_numpy(w.starts).to(dev),
+                             w.stages, w.steps, group=group)
+    q = q.cpu().numpy()[0].astype(np.float64)
+    assert math.degrees(wigner.geodesic_angle(q / np.linalg.norm(q), ref.q)) < 0.1
+
+
+@pytest.mark.parametrize("mode", [bh.BH_MODE_FP32, bh.BH_MODE_BF16_SPLIT])
+def test_full_path_pair16(dev, mode):
+    """Voxels -> GPU expansion -> GPU alignment vs the same in FP64; recovers R_true^{-1}."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    p = plan_for(16, 8, mode)
+    vols = torch.from_numpy(np.concatenate([w.template[None], w.vols])).to(dev)
+    c = bh.bh_expand(p, vols)
+    q, _ = bh.bh_align_batch(p, c[0].contiguous(), c[1:].contiguous(), torch.from_numpy(w.starts).to(dev),
+                             w.stages, w.steps)
+    q = q.cpu().numpy()[0].astype(np.float64)
+    q /= np.linalg.norm(q)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = oracle_align(w, 0, Bs, t, f)
+    assert math.degrees(wigner.geodesic_angle(q, ref.q)) < 0.1
+    assert math.degrees(wigner.geodesic_angle(q, wigner.quat_conj(w.q_true[0]))) < 1.0
+
+
+@pytest.mark.slow
+def test_align_batch32_sample(dev):
+    """1024 x 32^3 workload shape (l <= 16, 4-8-16, 16 starts, 30 steps): a sample of particles vs the oracle."""
+    w = synth.make_workload("batch32", count=4)
+    Bs = basis_for(32, 16)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    F = ball.expand(Bs, w.vols.astype(np.float64))
+    p = plan_for(32, 16, bh.BH_MODE_FP32)
+    q, s, sq, ss = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(F).to(dev), torch.from_numpy(w.starts).to(dev),
+                                     w.stages, w.steps, per_start=True)
+    q = q.cpu().numpy().astype(np.float64)
+    fails = []
+    for b in range(w.B):
+        ref = oracle_align(w, b, Bs, t, F[b])
+        ang = math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), ref.q))
+        # a near-tie between two distinct maxima (score gap < 1e-4 relative) may legitimately pick either
+        srt = np.sort(ref.start_score)[::-1]
+        tied = len(srt) > 1 and (srt[0] - srt[1]) < 1e-4 * abs(srt[0])
+        if ang >= 0.1 and not tied:
+            fails.append((b, ang))
+    assert not fails, fails
+
+
+def test_argument_errors(dev):
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    L = bh.lib()
+    st = (bh.ctypes.c_int * 2)(2, 2)  # not increasing
+    out = torch.zeros(8, device=dev)
+    assert L.bh_align_batch(p.handle, out.data_ptr(), out.data_ptr(), 1, out.data_ptr(), 1, st, 2, 1,
+                            out.data_ptr(), out.data_ptr(), None, 0) == bh.BH_ERR_ARG
+    st = (bh.ctypes.c_int * 1)(9)  # above Lmax
+    assert L.bh_align_batch(p.handle, out.data_ptr(), out.data_ptr(), 1, out.data_ptr(), 1, st, 1, 1,
+                            out.data_ptr(), out.data_ptr(), None, 0) == bh.BH_ERR_ARG
+    assert L.bh_score_grad(p.handle, out.data_ptr(), out.data_ptr(), 1, out.data_ptr(), 0, 2, out.data_ptr(), 0,
+                           0) == bh.BH_ERR_ARG
+    assert L.bh_expand(None, out.data_ptr(), 1, out.data_ptr(), 0) == bh.BH_ERR_ARG
+    assert b"plan" in L.bh_last_error()
