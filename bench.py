@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Throughput of ball-harmonic subtomogram alignment on GB300: subtomograms aligned per second.
+
+One step = the whole hot path over one batch of synthetic subtomograms already resident in HBM:
+expansion of every subtomogram into ball-harmonic coefficients (bh_expand) + multi-start marching
+gradient ascent over SO(3) with selection (bh_align_batch).  The template's coefficients are computed
+once before timing and stay resident.  Default workload: 1024 subtomograms of 32^3 (60-blob template,
+SNR 0.1, +-60 deg missing wedge), l <= 16, lambda <= 16 pi, marching 4 -> 8 -> 16, 16 starts, 30 steps.
+
+`value` is the chosen form (BF16 hi/lo tensor-core expansion + FP32 ascent); the plain FP32 form is
+timed in the same run and reported beside it with the median angle between the two forms' rotations.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+        (N > 1 is launched by torch.distributed.run: one independent replica per GPU, weak scaling.)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "subtomograms aligned/s at <=1 deg median angle error vs plain FP32; p50/p99 latency"
+UNIT = "subtomograms/s"
+L2_FLUSH_BYTES = 256 << 20
+# FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop per FMA per clock
+SMS, FMA_LANES = 152, 128
+
+
+def describe(w) -> str:
+    m = w.meta
+    parts = [f"{w.B} x {w.N}^3 subtomograms", f"{m['blobs']}-blob template sigma {m['sigma']}"]
+    if m["snr"] is not None:
+        parts.append(f"SNR {m['snr']}")
+    if m["wedge_deg"] is not None:
+        parts.append(f"+-{m['wedge_deg']:.0f} deg wedge")
+    parts += [f"l<={w.Lmax}", f"lambda<={w.N // 2}pi", "marching " + "-".join(map(str, w.stages)),
+              f"{w.S} starts", f"{w.steps} steps"]
+    return ", ".join(parts)
+
+
+def orbit_steps(L: int) -> int:
+    """Orbit-steps of one score+gradient evaluation at band L: sum_{m<=L} (2m+1)(L-m+1)."""
+    return sum((2 * m + 1) * (L - m + 1) for m in range(L + 1))
+
+
+# flop accounting of one orbit-step of the FP32 kernel (recursion coefficients 12, d and d' recursion 11,
+# eight accumulating FMAs 16): 39 flop
+FLOP_PER_ORBIT_STEP = 39
+
+
+def align_flops(w) -> float:
+    """FP32 flop of bh_align_batch on the workload: every start runs (1 + steps) evaluations per stage."""
+    per_start = sum((1 + w.steps) * orbit_steps(L) for L in w.stages)
+    return float(w.B) * w.S * per_start * FLOP_PER_ORBIT_STEP
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, reasons) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------------------ CPU oracle
+def _oracle_start(args):
+    """One start's marching ascent in FP64 (oracle), for the process pool."""
+    xi, q0, stages, steps = args
+    from oracle import align
+    return align.ascend(xi, q0, stages, steps).score
+
+
+def oracle_particle(pool, Bs, w, b, t_hat):
+    """Expansion + every start's ascent + selection of subtomogram b, starts spread over the pool."""
+    import numpy as np
+    from oracle import align, ball
+    f = ball.expand(Bs, w.vols[b].astype(np.float64))[0]
+    xi = align.build_xi(Bs, t_hat, f, max(w.stages))
+    jobs = [(xi, w.starts[b, s].astype(np.float64), w.stages, w.steps) for s in range(w.S)]
+    scores = pool.map(_oracle_start, jobs)
+    return align.select_best(np.array(scores))
+
+
+def oracle_pool(n):
+    import multiprocessing as mp
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    return mp.get_context("spawn").Pool(n)
+
+
+def cpu_workers(S: int) -> int:
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    return max(1, min(n, S))
+
+
+def cpu_baseline(w, n_particles: int = 8) -> dict:
+    """The FP64 oracle as it stands on the host cores: a bounded sample of the same workload."""
+    import numpy as np
+    from oracle import ball
+    Bs = ball.make_basis(w.Lmax, w.lam_max)
+    t_hat = ball.expand(Bs, w.template.astype(np.float64))[0]
+    workers = cpu_workers(w.S)
+    with oracle_pool(workers) as pool:
+        oracle_particle(pool, Bs, w, 0, t_hat)  # warm the workers
+        t0 = time.perf_counter()
+        for b in range(n_particles):
+            oracle_particle(pool, Bs, w, b, t_hat)
+        dt = time.perf_counter() - t0
+    return {"value": n_particles / dt, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{n_particles} subtomograms of the same workload (expansion + {w.S} starts x "
+                      f"marching {'-'.join(map(str, w.stages))} x {w.steps} steps + selection), FP64 numpy, "
+                      f"starts spread over {workers} processes"}
+
+
+# ------------------------------------------------------------------------------------------ arms
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step aligns one subtomogram of the workload on the host."""
+    from paper_2509_01180_gb300 import synth
+    if rank != 0:
+        return None
+    import numpy as np
+    from oracle import ball
+    w = synth.make_workload(args.workload, count=args.steps + args.warmup)
+    Bs = ball.make_basis(w.Lmax, w.lam_max)
+    t_hat = ball.expand(Bs, w.template.astype(np.float64))[0]
+    workers = cpu_workers(w.S)
+    with oracle_pool(workers) as pool:
+        for b in range(args.warmup):
+            oracle_particle(pool, Bs, w, b, t_hat)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            oracle_particle(pool, Bs, w, args.warmup + k, t_hat)
+        dt = time.perf_counter() - t0
+    value = args.steps / dt
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": describe(synth.make_workload(args.workload, count=1)) .replace("1 x", "per step 1 of"),
+                       "parallelism": "host processes"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": "one subtomogram per step (expansion + all starts + selection), FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ours(args, rank, world, device):
+    import numpy as np
+    import torch
+
+    from paper_2509_01180_gb300 import bh, synth
+
+    count = args.count
+    w = synth.make_workload(args.workload, count=count, first=rank * (count or 0))
+    B = w.B
+    forms = {"bf16split": bh.BH_MODE_BF16_SPLIT, "fp32": bh.BH_MODE_FP32}
+    order = [args.form] if args.form != "both" else ["bf16split", "fp32"]
+    stream = torch.cuda.current_stream(device)
+    vols = torch.from_numpy(w.vols).to(device)
+    starts = torch.from_numpy(w.starts).to(device)
+    tvol = torch.from_numpy(w.template[None]).to(device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    dist = world > 1
+    results = {}
+    for name in order:
+        t0 = time.perf_counter()
+        plan = bh.bh_plan_create(w.N, w.Lmax, w.lam_max, forms[name], max_batch=min(B, 4096))
+        plan_s = time.perf_counter() - t0
+        tmpl = bh.bh_expand(plan, tvol)[0].contiguous()
+        coeffs = torch.empty((B, plan.Nb, 2), dtype=torch.float32, device=device)
+        quat = torch.empty((B, 4), dtype=torch.float32, device=device)
+        score = torch.empty((B,), dtype=torch.float32, device=device)
+
+        def step():
+            bh.bh_expand(plan, vols, coeffs, stream=stream)
+            bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
+                              stream=stream)
+
+        for _ in range(args.warmup):
+            step()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        torch.cuda.synchronize(device)
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(device)
+        with ClockSampler(device.index if device.index is not None else 0) as clk:
+            for k in range(args.steps):
+                ev[k][0].record(stream)
+                bh.bh_expand(plan, vols, coeffs, stream=stream)
+                ev[k][1].record(stream)
+                bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
+                                  stream=stream)
+                ev[k][2].record(stream)
+                flush.zero_()  # evict L2 between timed steps (not timed)
+            torch.cuda.synchronize(device)
+        if dist:
+            torch.distributed.barrier()
+        t_exp = sum(e[0].elapsed_time(e[1]) for e in ev)
+        t_aln = sum(e[1].elapsed_time(e[2]) for e in ev)
+        t_tot = t_exp + t_aln
+        if dist:
+            tt = torch.tensor([t_tot, t_exp, t_aln], device=device)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            t_tot, t_exp, t_aln = [float(x) for x in tt]
+        q_res = quat.cpu().numpy().astype(np.float64)
+
+        # end to end through the public API: pinned host volumes in, rotations and scores out
+        hv = torch.from_numpy(w.vols).pin_memory()
+        hq = torch.empty((B, 4), dtype=torch.float32).pin_memory()
+        hs = torch.empty((B,), dtype=torch.float32).pin_memory()
+        dv = torch.empty_like(vols)
+        e2e_ms = 0.0
+        for k in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dv.copy_(hv, non_blocking=True)
+            bh.bh_expand(plan, dv, coeffs, stream=stream)
+            bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
+                              stream=stream)
+            hq.copy_(quat, non_blocking=True)
+            hs.copy_(score, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                e2e_ms += e0.elapsed_time(e1)
+            flush.zero_()
+        if dist:
+            tt = torch.tensor([e2e_ms], device=device)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(tt[0])
+        results[name] = {"plan_s": plan_s, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
+                         "clocks": clk.summary(), "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V,
+                         "h2d": int(hv.numel() * 4), "d2h": int(hq.numel() * 4 + hs.numel() * 4)}
+        plan.destroy()
+        del coeffs
+    return w, results
+
+
+def angle_deg(q1, q2):
+    import numpy as np
+    d = np.abs(np.sum(q1 * q2, axis=1) / (np.linalg.norm(q1, axis=1) * np.linalg.norm(q2, axis=1)))
+    return np.degrees(2 * np.arccos(np.clip(d, 0, 1)))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="batch32")
+    ap.add_argument("--count", type=int, default=None, help="subtomograms per GPU (default: the workload's)")
+    ap.add_argument("--form", choices=["both", "bf16split", "fp32"], default="both")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=device)
+
+    # the oracle's process pool is spawned before the first GPU call
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from paper_2509_01180_gb300 import synth
+        base = cpu_baseline(synth.make_workload(args.workload, count=8))
+
+    w, res = run_ours(args, rank, world, device)
+    if rank == 0:
+        main_form = "bf16split" if "bf16split" in res else next(iter(res))
+        r = res[main_form]
+        B = w.B
+        value = world * B / (r["t_tot"] / args.steps / 1e3)
+        peaks = measured_peaks()
+        clocks = r["clocks"]
+        # dominant kernel roofline
+        per_step_exp, per_step_aln = r["t_exp"] / args.steps, r["t_aln"] / args.steps
+        if per_step_aln >= per_step_exp:
+            fl = align_flops(w)
+            f_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+            peak = SMS * FMA_LANES * 2 * f_ghz * 1e9 / 1e12
+            ach = fl / (per_step_aln / 1e3) / 1e12
+            roof = {"kernel": "k_align (bh_align_batch)", "bound": "alu", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": f"FP32 FMA: {SMS} SMs x {FMA_LANES} lanes x 2 flop x {f_ghz * 1e3:.0f} MHz"}
+        else:
+            mult = 3 if main_form == "bf16split" else 1
+            fl = 2.0 * B * r["V"] * r["Nb"] * mult
+            peak = peaks.get("bf16_tflops", 1900.0) if main_form == "bf16split" else \
+                SMS * FMA_LANES * 2 * (peaks.get("sm_max_mhz") or 2070.0) / 1e6
+            ach = fl / (per_step_exp / 1e3) / 1e12
+            roof = {"kernel": "bh_expand (gather + GEMM + complex)", "bound": "tensor" if mult == 3 else "alu",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": "MEASURED_PEAKS bf16_tflops (burst)" if mult == 3 else "FP32 FMA peak"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["t_tot"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16-split/fp32" if main_form == "bf16split" else "fp32", "data": "synthetic",
+            "config": {"workload": describe(w), "form": main_form,
+                       "expansion": "tcgen05 BF16 hi/lo split, FP32 accumulate" if main_form == "bf16split"
+                       else "FP32 FFMA", "ascent": "FP32", "l2": "flushed between timed steps (256 MB write)",
+                       "template": "expanded once before timing (resident)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "breakdown_ms_per_step": {"expand": per_step_exp, "align": per_step_aln, "plan_create_s": r["plan_s"]},
+            "roofline": roof,
+            "clocks": clocks,
+            "e2e": {"value": world * B / (r["e2e_ms"] / args.steps / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+            "gpu_launches": 4 * args.steps * max(1, math.ceil(B / min(B, 4096))),
+        }
+        qt_inv = w.q_true * np.array([1, -1, -1, -1])
+        acc = {"median_angle_vs_truth_deg": float(np.median(angle_deg(r["q"], qt_inv)))}
+        if "fp32" in res and main_form != "fp32":
+            f = res["fp32"]
+            acc["median_angle_vs_fp32_deg"] = float(np.median(angle_deg(r["q"], f["q"])))
+            line["plain_fp32"] = {"value": world * B / (f["t_tot"] / args.steps / 1e3),
+                                  "ms_per_step": f["t_tot"] / args.steps,
+                                  "breakdown_ms_per_step": {"expand": f["t_exp"] / args.steps,
+                                                            "align": f["t_aln"] / args.steps},
+                                  "median_angle_vs_truth_deg": float(np.median(angle_deg(f["q"], qt_inv)))}
+        line["accuracy"] = acc
+        if base is not None:
+            line["cpu_baseline"] = base
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -70,7 +70,7 @@ def test_expand_matches_oracle(dev, mode, N, L, B, max_batch):
     for b in range(B):
         assert rel_l2(got[b], ref[b]) < 1e-4, (b, rel_l2(got[b], ref[b]))
     if mode == bh.BH_MODE_FP32:
-        assert rel_l2(got, ref) < 2e-6
+        assert rel_l2(got, ref) < 1e-5  # K ~ 1.7e4-term FP32 sums
 
 
 @pytest.mark.parametrize("mode", [bh.BH_MODE_FP32, bh.BH_MODE_BF16_SPLIT])
