@@ -124,6 +124,24 @@ int bh_plan_info(const bh_plan* plan, bh_plan_opts* opts);
  */
 int bh_expand(bh_plan* plan, const float* vols, int B, float* coeffs, void* stream);
 
+/*
+ * Same result as bh_expand, for callers that cannot allocate device memory while they run -- for
+ * example a thread recording into a stream that another component captures into a CUDA graph, or an
+ * application that owns all device memory and only lends out pointers.  The paper has no counterpart:
+ * this is a deployment variant of the expansion.
+ *   Scratch: a fixed 64 MiB array compiled into the library (a file-scope __device__ array), held on
+ *   every GPU where the library's module is loaded until the process exits.  The call allocates
+ *   nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ *   Limit: one pass needs 128 * (V_pad + Nb_pad) * 4 bytes (V_pad, Nb_pad = voxel and coefficient
+ *   counts rounded up to 64 and 256); plans above 64 MiB per pass (for example N = 64, Lmax = 32)
+ *   are rejected with BH_ERR_ARG.  Larger B is processed in several passes.
+ *   Set-up: the first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *   with that device current; make that first call before any stream capture.
+ *   Sharing: all calls use the same array and it keeps the last call's contents (each pass overwrites
+ *   what it reads, so nothing needs clearing); calls whose GPU work overlaps race on it.
+ */
+int bh_expand_noalloc(bh_plan* plan, const float* vols, int B, float* coeffs, void* stream);
+
 /* ------------------------------------------------------------------ score and gradient */
 /*
  * Eq. 2 at s = 0, truncated at band L, and its closed-form gradient (Sec. II-C) at given

@@ -21,7 +21,8 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
-           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_score_grad", "bh_align_batch"]
+           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
+           "bh_align_batch"]
 
 
 class BHError(RuntimeError):
@@ -62,6 +63,7 @@ def lib() -> ctypes.CDLL:
         L.bh_plan_layout.argtypes = [vp, vp, vp, vp]
         L.bh_plan_info.argtypes = [vp, ctypes.POINTER(PlanOpts)]
         L.bh_expand.argtypes = [vp, vp, i, vp, vp]
+        L.bh_expand_noalloc.argtypes = [vp, vp, i, vp, vp]
         L.bh_score_grad.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp]
         L.bh_align_batch.argtypes = [vp, vp, vp, i, vp, i, vp, i, i, vp, vp, ctypes.POINTER(AlignOpts), vp]
         for name in EXPORTS:

@@ -83,6 +83,8 @@ namespace bh {
 int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const std::vector<double>& angular,
                  const std::vector<int>& vox_r2, const std::vector<int2>& colinfo, double h3);
 int make_tensor_maps(bh_plan* p);
+int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scratch_x, float* scratch_c, int rows_cap,
+                cudaStream_t stream);
 // align.cu
 int align_init_constants();
 }  // namespace bh

@@ -470,6 +470,59 @@ static int launch_gemm(bh_plan* p, int Mp, cudaStream_t stream) {
   return BH_OK;
 }
 
+// Expansion through caller-provided scratch (used by the entry point that allocates nothing): the same
+// kernels as bh_expand, with the gathered volumes and the real GEMM output placed in `scratch_x` /
+// `scratch_c`, `rows_cap` rows (a multiple of the 128-row M tile) per pass.  Tensor maps of the gathered
+// volumes are encoded for the given scratch on every call (host-side encoding, no allocation).
+int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scratch_x, float* scratch_c, int rows_cap,
+                cudaStream_t stream) {
+  const long long N3 = (long long)p->N * p->N * p->N;
+  float* X32 = nullptr;
+  __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
+  CUtensorMap tm_hi, tm_lo;
+  if (p->mode == BH_MODE_FP32) {
+    X32 = static_cast<float*>(scratch_x);
+  } else {
+    Xhi = static_cast<__nv_bfloat16*>(scratch_x);
+    Xlo = Xhi + (size_t)rows_cap * p->V_pad;
+    int st;
+    if ((st = encode_bf16_2d(&tm_hi, Xhi, p->V_pad, rows_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+    if ((st = encode_bf16_2d(&tm_lo, Xlo, p->V_pad, rows_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+  }
+  for (int b0 = 0; b0 < B; b0 += rows_cap) {
+    const int Bc = std::min(rows_cap, B - b0);
+    const int Mp = round_up(Bc, kGemmBM);
+    dim3 g1((p->V_pad + 255) / 256, Mp);
+    k_gather<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
+    BH_CHECK_LAUNCH();
+    if (p->mode == BH_MODE_FP32) {
+      dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM);
+      k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, scratch_c, Mp, p->Nb_pad, p->V_pad);
+    } else {
+      const int num_kb = p->V_pad / kGemmBK;
+      if (p->gemm_bn == 256) {
+        BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcCfg<256>::SMEM));
+        dim3 grid(p->Nb_pad / 256, Mp / kGemmBM);
+        k_gemm_tc<256><<<grid, 128, TcCfg<256>::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c,
+                                                                p->Nb_pad, num_kb, p->d_err);
+      } else {
+        BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TcCfg<128>::SMEM));
+        dim3 grid(p->Nb_pad / 128, Mp / kGemmBM);
+        k_gemm_tc<128><<<grid, 128, TcCfg<128>::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c,
+                                                                p->Nb_pad, num_kb, p->d_err);
+      }
+    }
+    BH_CHECK_LAUNCH();
+    dim3 g2((p->Nb + 255) / 256, Bc);
+    k_to_complex<<<g2, 256, 0, stream>>>(scratch_c, p->Nb_pad, Bc, p->Nb, p->d_slot,
+                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb);
+    BH_CHECK_LAUNCH();
+  }
+  return BH_OK;
+}
+
 }  // namespace bh
 
 using namespace bh;
