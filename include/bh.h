@@ -189,6 +189,75 @@ int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int
                    const float* starts, int S, const int* stages, int nstages, int steps,
                    float* quat_out, float* score_out, const bh_align_opts* opts, void* stream);
 
+/* ------------------------------------------------------------------ random starts */
+/*
+ * Uniform random rotations for the multi-start ascent (the paper starts from local maxima of the
+ * lowest band instead; uniform starts are this library's default).  Host only.  Start s of
+ * subtomogram b depends only on (seed, b, s): three uniforms from SplitMix64 at counters
+ * seed + 3 (b S + s) + {0,1,2}, mapped by Shoemake's method to a unit quaternion with w >= 0.
+ *   out  host, B * S * 4 floats, layout [b][s][w,x,y,z].
+ */
+int bh_random_starts(uint64_t seed, int B, int S, float* out);
+
+/* ------------------------------------------------------------------ serving */
+/*
+ * A request loop with continuous batching: requests of uneven sizes and box edges arrive at any
+ * time; a worker thread admits them in arrival order while the HBM budget and a free stream slot
+ * allow, merges waiting requests of the same box edge into one batch (expansion + one alignment
+ * launch with a per-subtomogram template index), and keeps up to max_inflight batches on the device
+ * at once on separate streams.  Template coefficients stay resident.  Each subtomogram's result
+ * depends only on its own data, template, starts and the box's schedule -- not on what it was
+ * batched with.  Schedule per box edge N: Lmax = N/2, lambda_max = pi N/2, bands Lmax/4, Lmax/2,
+ * Lmax, `steps` ascent steps per band.
+ */
+typedef struct bh_server bh_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device bytes for in-flight batches (plans and templates excluded); 0 = 8 GiB */
+  int max_inflight;        /* batches on the device at once (one stream each): 1..16; 0 = 4 */
+  int max_batch;           /* subtomograms merged into one batch: 1..65536; 0 = 1024 */
+  int queue_capacity;      /* requests waiting for admission; 0 = 65536 */
+  int mode;                /* BH_MODE_* of the expansion for every box edge */
+  int steps;               /* ascent steps per band; 0 = 30 */
+} bh_serve_opts;
+
+typedef struct {
+  int template_id;     /* from bh_serve_add_template; fixes the box edge N */
+  int B;               /* subtomograms, >= 1 */
+  const float* vols;   /* host, B * N^3 floats [b][z][y][x]; must stay valid until the request completes */
+  int S;               /* starts per subtomogram, 1..512 */
+  const float* starts; /* host, B * S * 4 floats, or NULL: bh_random_starts(seed, B, S) */
+  uint64_t seed;
+  float* quat_out;     /* host, B * 4 floats, written before bh_serve_poll reports BH_OK */
+  float* score_out;    /* host, B floats */
+} bh_request;
+
+typedef struct {
+  uint64_t submitted, completed, batches;
+  uint64_t queued;          /* waiting for admission */
+  uint64_t inflight_batches;
+  size_t inflight_bytes;    /* budget in use */
+} bh_serve_counters;
+
+/* Create a server on the current device.  Errors: BH_ERR_ARG, BH_ERR_CUDA, BH_ERR_UNSUPPORTED. */
+int bh_serve_create(bh_server** out, const bh_serve_opts* opts);
+/* Expand a template volume (host, N^3 floats) once and keep its coefficients resident; builds the
+ * plan of box edge N on first use.  Synchronous.  *template_id receives its id. */
+int bh_serve_add_template(bh_server* srv, int N, const float* vol, int* template_id);
+/* Queue a request (non-blocking).  BH_ERR_BUDGET if its footprint alone exceeds the budget,
+ * BH_ERR_BUSY if the queue is full, BH_ERR_ARG for malformed requests. */
+int bh_serve_submit(bh_server* srv, const bh_request* req, uint64_t* ticket);
+/* BH_OK once the request's outputs are written (latency_ms, may be NULL: submit to completion),
+ * BH_PENDING before; BH_ERR_ARG for an unknown ticket; BH_ERR_CUDA if its batch failed. */
+int bh_serve_poll(bh_server* srv, uint64_t ticket, double* latency_ms);
+/* Like poll, blocking up to timeout_ms (< 0: forever); BH_ERR_TIMEOUT when the time runs out. */
+int bh_serve_wait(bh_server* srv, uint64_t ticket, double timeout_ms, double* latency_ms);
+/* Hold (1) or resume (0) admission of queued requests; work already admitted continues. */
+int bh_serve_pause(bh_server* srv, int paused);
+int bh_serve_stats(bh_server* srv, bh_serve_counters* out);
+/* Finish admitted work, drop queued requests, free everything.  NULL is accepted. */
+int bh_serve_destroy(bh_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,8 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
-           "bh_align_batch"]
+           "bh_align_batch", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
 class BHError(RuntimeError):
@@ -69,6 +70,7 @@ def lib() -> ctypes.CDLL:
         for name in EXPORTS:
             if name not in ("bh_last_error", "bh_status_string"):
                 getattr(L, name).restype = i
+        _serve_sigs(L)
         _lib = L
     return _lib
 
@@ -210,3 +212,120 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     if per_start:
         return quat, score, sq, ss
     return quat, score
+
+
+# ------------------------------------------------------------------ random starts
+def bh_random_starts(seed: int, B: int, S: int) -> np.ndarray:
+    """(B, S, 4) float32 uniform rotations, SplitMix64 + Shoemake (host)."""
+    out = np.empty((B, S, 4), dtype=np.float32)
+    _check(lib().bh_random_starts(ctypes.c_uint64(seed), B, S, out.ctypes.data), "bh_random_starts")
+    return out
+
+
+# ------------------------------------------------------------------ serving
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("template_id", ctypes.c_int), ("B", ctypes.c_int), ("vols", ctypes.c_void_p), ("S", ctypes.c_int),
+                ("starts", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("quat_out", ctypes.c_void_p),
+                ("score_out", ctypes.c_void_p)]
+
+
+class ServeCounters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("inflight_batches", ctypes.c_uint64), ("inflight_bytes", ctypes.c_size_t)]
+
+
+def _serve_sigs(L):
+    vp, i = ctypes.c_void_p, ctypes.c_int
+    if getattr(L, "_serve_ready", False):
+        return
+    L.bh_random_starts.argtypes = [ctypes.c_uint64, i, i, vp]
+    L.bh_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeOpts)]
+    L.bh_serve_add_template.argtypes = [vp, i, vp, ctypes.POINTER(i)]
+    L.bh_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.bh_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+    L.bh_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.bh_serve_pause.argtypes = [vp, i]
+    L.bh_serve_stats.argtypes = [vp, ctypes.POINTER(ServeCounters)]
+    L.bh_serve_destroy.argtypes = [vp]
+    for n in ("bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
+              "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"):
+        getattr(L, n).restype = i
+    L._serve_ready = True
+
+
+class Server:
+    """Owns a bh_server handle; keeps every request's host arrays alive until it completes."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self._live = {}
+
+    def add_template(self, vol: np.ndarray) -> int:
+        vol = np.ascontiguousarray(vol, dtype=np.float32)
+        tid = ctypes.c_int()
+        _check(lib().bh_serve_add_template(self.handle, vol.shape[0], vol.ctypes.data, ctypes.byref(tid)),
+               "bh_serve_add_template")
+        return tid.value
+
+    def submit(self, template_id: int, vols: np.ndarray, S: int, starts: np.ndarray | None = None, seed: int = 0) -> int:
+        """Queue a request; returns its ticket (BHError with BH_ERR_BUDGET / BH_ERR_BUSY / BH_ERR_ARG)."""
+        vols = np.ascontiguousarray(vols, dtype=np.float32)
+        B = vols.shape[0]
+        q = np.zeros((B, 4), dtype=np.float32)
+        sc = np.zeros((B,), dtype=np.float32)
+        st = None if starts is None else np.ascontiguousarray(starts, dtype=np.float32)
+        r = Request(template_id, B, vols.ctypes.data, S, 0 if st is None else st.ctypes.data, seed, q.ctypes.data,
+                    sc.ctypes.data)
+        t = ctypes.c_uint64()
+        _check(lib().bh_serve_submit(self.handle, ctypes.byref(r), ctypes.byref(t)), "bh_serve_submit")
+        self._live[t.value] = (vols, st, q, sc)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (quat (B,4), score (B,), latency_ms)."""
+        lat = ctypes.c_double()
+        st = lib().bh_serve_poll(self.handle, ticket, ctypes.byref(lat))
+        if st == BH_PENDING:
+            return None
+        _check(st, "bh_serve_poll")
+        _, _, q, sc = self._live.pop(ticket)
+        return q, sc, lat.value
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0):
+        lat = ctypes.c_double()
+        _check(lib().bh_serve_wait(self.handle, ticket, float(timeout_ms), ctypes.byref(lat)), "bh_serve_wait")
+        _, _, q, sc = self._live.pop(ticket)
+        return q, sc, lat.value
+
+    def pause(self, paused: bool) -> None:
+        _check(lib().bh_serve_pause(self.handle, 1 if paused else 0), "bh_serve_pause")
+
+    def stats(self) -> dict:
+        c = ServeCounters()
+        _check(lib().bh_serve_stats(self.handle, ctypes.byref(c)), "bh_serve_stats")
+        return {k: getattr(c, k) for k, _ in ServeCounters._fields_}
+
+    def destroy(self) -> None:
+        if self.handle:
+            lib().bh_serve_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def bh_serve_create(hbm_budget_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0, queue_capacity: int = 0,
+                    mode: int = BH_MODE_BF16_SPLIT, steps: int = 0) -> Server:
+    L = lib()
+    o = ServeOpts(hbm_budget_bytes, max_inflight, max_batch, queue_capacity, mode, steps)
+    h = ctypes.c_void_p()
+    _check(L.bh_serve_create(ctypes.byref(h), ctypes.byref(o)), "bh_serve_create")
+    return Server(h.value)

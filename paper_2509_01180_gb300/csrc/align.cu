@@ -10,16 +10,19 @@
 // Folding (real volumes, so xi^l_{-m,-n} = (-1)^{m+n} conj(xi^l_{mn})), and d^l_{nm} = (-1)^{m-n} d^l_{mn}:
 // the four pairs (m,n), (n,m), (-m,-n), (-n,-m) share one recursion, and (-m,-n) contributes what
 // (m,n) contributes.  An "orbit" (m,n) with m >= |n| therefore carries two slots (m,n) and (n,m) with
-// weights 2 (1 for (0,0), slot (n,m) dropped on the diagonals n = +-m).  Its entries for l = m..Lb
-// are stored contiguously in shared memory as float4 (w1 xi_mn, w2 (-1)^{m-n} xi_nm).
+// weights 2 (1 for (0,0), slot (n,m) dropped on the diagonals n = +-m).  Row m of the shared-memory
+// table holds, for l = m..Lb and n = -m..m (n fastest), the float4 P_l (w1 xi_mn, w2 (-1)^{m-n} xi_nm).
 //
-// d^l_{mn}(beta) for l >= m >= |n| by the three-term recursion in l,
+// d^l_{mn}(beta) for l >= m >= |n| obeys the three-term recursion in l
 //   d^l = A_l (cos beta - B_l) d^{l-1} - C_l d^{l-2},
 //   A_l = l(2l-1)/u_l, B_l = m n /(l(l-1)), C_l = l u_{l-1} / ((l-1) u_l), u_l = sqrt((l^2-m^2)(l^2-n^2)),
-// started from the closed form d^m_{mn} = (-1)^{m-n} sqrt(C(2m, m+n)) cos(beta/2)^{m+n} sin(beta/2)^{m-n},
-// and its beta-derivative by differentiating the same recursion.  The Euler angles never appear
-// explicitly: cos(beta/2) = |(w,z)|, sin(beta/2) = |(x,y)|, e^{i(alpha+gamma)/2} = (w + i z)/cos(beta/2),
-// e^{i(alpha-gamma)/2} = (y - i x)/sin(beta/2).
+// from the closed form d^m_{mn} = (-1)^{m-n} sqrt(C(2m, m+n)) cos(beta/2)^{m+n} sin(beta/2)^{m-n}.
+// Writing d^l = P_l e^l with P_l = prod_{j=m+1..l} j(2j-1)/u_j (independent of beta, folded into the
+// table) turns it into a recursion with rational coefficients and no square root:
+//   e^l = (cos beta - B_l) e^{l-1} - g_l e^{l-2},  g_l = ((l-1)^2-m^2)((l-1)^2-n^2) / ((l-1)^2 (2l-1)(2l-3)),
+// and its beta-derivative  e'^l = (cos beta - B_l) e'^{l-1} - sin beta e^{l-1} - g_l e'^{l-2}.
+// The Euler angles never appear explicitly: cos(beta/2) = |(w,z)|, sin(beta/2) = |(x,y)|,
+// e^{i(alpha+gamma)/2} = (w + i z)/cos(beta/2), e^{i(alpha-gamma)/2} = (y - i x)/sin(beta/2).
 //
 // Gradient along right perturbations R exp(eps J_i) (body axes): from dS/dalpha, dS/dbeta, dS/dgamma
 // with the ZYZ body angular velocity  omega = alpha'(-sb cg, sb sg, cb) + beta'(sg, cg, 0) + gamma'(0,0,1):
@@ -37,8 +40,6 @@ namespace bh {
 namespace {
 
 constexpr int kBinStride = 2 * kMaxL + 1;
-__constant__ float4 c_lconst[kMaxL + 2];                   // (l(2l-1), (2l-1)/(l-1), l/(l-1), 0)
-__constant__ float c_lbin[(kMaxL + 1) * kBinStride];       // 0.5 log2 C(2m, m+n) at [m][m+n]
 
 constexpr int kMaxStages = 8;
 constexpr int kMaxThreads = 512;  // threads per CTA (S * G rounded up to a warp)
@@ -56,6 +57,9 @@ struct AlignArgs {
   int stages[kMaxStages];
   int steps;
   int Lb;  // band of the shared-memory table
+  const float* P;       // [orbit table of band Lmax] P_l(m,n) = prod_{j=m+1..l} j(2j-1)/u_j
+  const float2* coef;   // [orbit table of band Lmax] (B_l, g_l) of the rescaled recursion
+  const float* lbin;    // [m][m+n] 0.5 log2 C(2m, m+n), row stride 2 kMaxL + 1
   float4* quat_out;
   float* score_out;
   float4* start_quat_out;
@@ -91,29 +95,30 @@ __device__ __forceinline__ float4 qmul(float4 a, float4 b) {
 
 // Orbit table of one subtomogram (see header comment) for l <= Lb.
 __device__ void build_table(float4* __restrict__ tab, const Layout& lay, const float2* __restrict__ tmpl,
-                            const float2* __restrict__ sub, int Lb, int tid, int nth) {
+                            const float2* __restrict__ sub, const float* __restrict__ P, int Lb, int tid, int nth) {
   const int nent = tab_base(Lb + 1, Lb);
   for (int e = tid; e < nent; e += nth) {
     int m = 0;
     while (tab_base(m + 1, Lb) <= e) ++m;
-    const int len = Lb - m + 1;
+    const int w = 2 * m + 1;
     const int rem = e - tab_base(m, Lb);
-    const int n = rem / len - m, l = m + rem % len;
-    const int K = lay.K[l], off = lay.off[l], w = 2 * l + 1;
+    const int l = m + rem / w, n = rem % w - m;
+    const int K = lay.K[l], off = lay.off[l], wl = 2 * l + 1;
     const bool two = (m > 0) && (n != m) && (n != -m);
     float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);
     for (int k = 0; k < K; ++k) {
-      const float2 tm = __ldg(tmpl + off + k * w + m + l), fn = __ldg(sub + off + k * w + n + l);
+      const float2 tm = __ldg(tmpl + off + k * wl + m + l), fn = __ldg(sub + off + k * wl + n + l);
       x1.x += tm.x * fn.x + tm.y * fn.y;
       x1.y += tm.x * fn.y - tm.y * fn.x;
       if (two) {
-        const float2 tn = __ldg(tmpl + off + k * w + n + l), fm = __ldg(sub + off + k * w + m + l);
+        const float2 tn = __ldg(tmpl + off + k * wl + n + l), fm = __ldg(sub + off + k * wl + m + l);
         x2.x += tn.x * fm.x + tn.y * fm.y;
         x2.y += tn.x * fm.y - tn.y * fm.x;
       }
     }
-    const float w1 = (m == 0) ? 1.f : 2.f;
-    const float w2 = two ? (((m - n) & 1) ? -2.f : 2.f) : 0.f;
+    const float pl = __ldg(P + tab_base(m, lay.Lmax) + (l - m) * w + (n + m));
+    const float w1 = ((m == 0) ? 1.f : 2.f) * pl;
+    const float w2 = two ? (((m - n) & 1) ? -2.f : 2.f) * pl : 0.f;
     tab[e] = make_float4(w1 * x1.x, w1 * x1.y, w2 * x2.x, w2 * x2.y);
   }
 }
@@ -125,15 +130,17 @@ struct Eval {
 // Score and body-frame gradient of rotation q at band L (FP32), from the orbit table of band Lb >= L.
 // Every lane of a G-group returns the same (bitwise) result.
 template <int G>
-__device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg) {
+__device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg,
+                              const float2* __restrict__ coef, const float* __restrict__ lbin, int Lmax) {
   const float w = q.x, x = q.y, y = q.z, z = q.w;
   const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
   const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);   // e^{i(alpha+gamma)/2}
   const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);  // e^{i(alpha-gamma)/2}
   const float xb = (cb - sb) * (cb + sb);                                             // cos beta
   const float sinb = 2.f * cb * sb;                                                   // sin beta
-  const float lc = cb > 0.f ? fmaxf(log2f(cb), -500.f) : -500.f;
-  const float ls = sb > 0.f ? fmaxf(log2f(sb), -500.f) : -500.f;
+  const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
+  const float lcc = log2f(cbc), lss = log2f(sbc);
+  const float rcs = cbc / sbc, rsc = sbc / cbc;
   const float2 Es = cconj(es);
   const float2 EsG = cpow(Es, G), edG = cpow(ed, G);
   const float2 Ed = cconj(ed);
@@ -142,48 +149,66 @@ __device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, flo
   float2 Wrow = cpow(ed, qg);
   float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
   for (int m = 0; m <= L; ++m) {
-    const int len = Lb - m + 1;
+    const int w = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
+    const float2* crow = coef + tab_base(m, Lmax);
     float2 U = Uq, W = Wrow;
     for (int n = qg - m; n <= m; n += G) {
-      const float4* e = rowp + (n + m) * len;
-      const float lb = c_lbin[m * kBinStride + m + n];
-      const float sg = ((m - n) & 1) ? -1.f : 1.f;
+      // seed at l = m: d = sg 2^lb c^(m+n) s^(m-n), c = cos(beta/2), s = sin(beta/2) (both clamped to
+      // >= 1e-30, which changes no value above the FP32 underflow), and its beta-derivative
+      // d' = d ((m-n) c/s - (m+n) s/c) / 2
+      const float lb = __ldg(lbin + m * kBinStride + m + n);
       const float fa = (float)(m + n), fd = (float)(m - n);
-      const float d = sg * exp2f(lb + fa * lc + fd * ls);
-      float dp = 0.f;
-      if (m != n) dp += 0.5f * fd * exp2f(lb + (fa + 1.f) * lc + (fd - 1.f) * ls);
-      if (m + n != 0) dp -= 0.5f * fa * exp2f(lb + (fa - 1.f) * lc + (fd + 1.f) * ls);
-      dp *= sg;
-      float4 xv = e[0];
+      float d = exp2f(lb + fa * lcc + fd * lss);
+      d = ((m - n) & 1) ? -d : d;
+      const float dp = 0.5f * d * (fd * rcs - fa * rsc);
+      const float4* ep = rowp + (n + m);
+      const float2* kp = crow + (n + m);
+      float4 xv = *ep;
       float a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
       float b1r = dp * xv.x, b1i = dp * xv.y, b2r = dp * xv.z, b2i = dp * xv.w;
-      float d1 = d, d2 = 0.f, p1 = dp, p2 = 0.f, uprev = 0.f;
-      const float fm2 = (float)(m * m), fn2 = (float)(n * n), fmn = (float)(m * n);
-      for (int l = m + 1; l <= L; ++l) {
-        const float fl2 = (float)(l * l);
-        const float pp = (fl2 - fm2) * (fl2 - fn2);
-        const float iu = rsqrtf(pp);
-        const float4 k = c_lconst[l];
-        const float A = k.x * iu, AB = k.y * fmn * iu, Cc = k.z * uprev * iu;
-        uprev = pp * iu;
-        const float t = fmaf(A, xb, -AB);
-        const float dn = fmaf(t, d1, -Cc * d2);
-        const float pn = fmaf(t, p1, fmaf(-Cc, p2, -A * sinb * d1));
-        d2 = d1;
-        d1 = dn;
-        p2 = p1;
-        p1 = pn;
-        xv = e[l - m];
-        a1r = fmaf(dn, xv.x, a1r);
-        a1i = fmaf(dn, xv.y, a1i);
-        a2r = fmaf(dn, xv.z, a2r);
-        a2i = fmaf(dn, xv.w, a2i);
-        b1r = fmaf(pn, xv.x, b1r);
-        b1i = fmaf(pn, xv.y, b1i);
-        b2r = fmaf(pn, xv.z, b2r);
-        b2i = fmaf(pn, xv.w, b2i);
+      float e1 = d, e2 = 0.f, p1 = dp, p2 = 0.f;
+      int l = m + 1;
+#define BH_ORBIT_STEP(E_NEW, P_NEW, E1, E2, P1, P2, K, X)                   \
+  {                                                                        \
+    const float t_ = xb - (K).x;                                           \
+    E_NEW = fmaf(t_, E1, -(K).y * E2);                                     \
+    P_NEW = fmaf(t_, P1, -fmaf(sinb, E1, (K).y * P2));                     \
+    a1r = fmaf(E_NEW, (X).x, a1r);                                         \
+    a1i = fmaf(E_NEW, (X).y, a1i);                                         \
+    a2r = fmaf(E_NEW, (X).z, a2r);                                         \
+    a2i = fmaf(E_NEW, (X).w, a2i);                                         \
+    b1r = fmaf(P_NEW, (X).x, b1r);                                         \
+    b1i = fmaf(P_NEW, (X).y, b1i);                                         \
+    b2r = fmaf(P_NEW, (X).z, b2r);                                         \
+    b2i = fmaf(P_NEW, (X).w, b2i);                                         \
+  }
+      for (; l + 1 <= L; l += 2) {
+        ep += w;
+        kp += w;
+        const float2 k0 = __ldg(kp);
+        const float4 x0 = *ep;
+        ep += w;
+        kp += w;
+        const float2 k1 = __ldg(kp);
+        const float4 x1 = *ep;
+        float ea, pa, eb, pb;
+        BH_ORBIT_STEP(ea, pa, e1, e2, p1, p2, k0, x0);
+        BH_ORBIT_STEP(eb, pb, ea, e1, pa, p1, k1, x1);
+        e2 = ea;
+        e1 = eb;
+        p2 = pa;
+        p1 = pb;
       }
+      if (l <= L) {
+        ep += w;
+        kp += w;
+        const float2 k0 = __ldg(kp);
+        const float4 x0 = *ep;
+        float ea, pa;
+        BH_ORBIT_STEP(ea, pa, e1, e2, p1, p2, k0, x0);
+      }
+#undef BH_ORBIT_STEP
       const float2 P1 = cmul(U, W), P2 = cmul(U, cconj(W));
       const float2 z1 = cmul(P1, make_float2(a1r, a1i)), z2 = cmul(P2, make_float2(a2r, a2i));
       S += z1.x + z2.x;
@@ -219,15 +244,20 @@ __device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p)
   return a.tmpl + (size_t)t * a.lay.Nb;
 }
 
-// Multi-start marching ascent; one CTA per subtomogram, blockDim = roundup(S*G, 32).
-template <int G>
-__global__ void __launch_bounds__(512) k_align(const AlignArgs a) {
+// Minimum resident CTAs per SM requested from the compiler for a block of NT threads: enough that the
+// register budget allows >= 7 small CTAs (shared memory allows 7 orbit tables of band 16 per SM).
+__host__ __device__ constexpr int min_blocks(int NT) { return NT <= 64 ? 8 : NT <= 128 ? 7 : NT <= 256 ? 3 : 1; }
+
+// Multi-start marching ascent; one CTA per subtomogram, blockDim = NT = roundup(S*G, 32).
+template <int G, int NT>
+__global__ void __launch_bounds__(NT, min_blocks(NT)) k_align(const AlignArgs a) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
   const int s = threadIdx.x / G, qg = threadIdx.x % G;
   const bool active = s < a.S;
   const int se = active ? s : s % a.S;  // lanes past the last start shadow a real one and write nothing
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.Lb, threadIdx.x, blockDim.x);
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
   __syncthreads();
 
   float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
@@ -238,7 +268,7 @@ __global__ void __launch_bounds__(512) k_align(const AlignArgs a) {
     const int L = a.stages[st];
     const float hmax = 3.14159265358979f / (float)L;
     float h = 0.5f * hmax;
-    cur = eval_rotation<G>(smem_tab, a.Lb, L, q, qg);
+    cur = eval_rotation<G>(smem_tab, a.Lb, L, q, qg, a.coef, a.lbin, a.lay.Lmax);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -247,7 +277,7 @@ __global__ void __launch_bounds__(512) k_align(const AlignArgs a) {
       sincosf(stop ? 0.f : 0.5f * h, &sh, &ch);
       const float4 dq = make_float4(ch, sh * cur.gx * inv, sh * cur.gy * inv, sh * cur.gz * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const Eval tr = eval_rotation<G>(smem_tab, a.Lb, L, qt, qg);
+      const Eval tr = eval_rotation<G>(smem_tab, a.Lb, L, qt, qg, a.coef, a.lbin, a.lay.Lmax);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -280,16 +310,17 @@ __global__ void __launch_bounds__(512) k_align(const AlignArgs a) {
 
 // Score and gradient at given rotations; one CTA per subtomogram.
 template <int G>
-__global__ void __launch_bounds__(512) k_score(const AlignArgs a, int L) {
+__global__ void __launch_bounds__(512, 1) k_score(const AlignArgs a, int L) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
   const int s = threadIdx.x / G, qg = threadIdx.x % G;
   const bool active = s < a.S;
   const int se = active ? s : s % a.S;
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.Lb, threadIdx.x, blockDim.x);
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
   __syncthreads();
   const float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
-  const Eval r = eval_rotation<G>(smem_tab, a.Lb, L, q, qg);
+  const Eval r = eval_rotation<G>(smem_tab, a.Lb, L, q, qg, a.coef, a.lbin, a.lay.Lmax);
   if (active && qg == 0) {
     a.score_out[(size_t)p * a.S + s] = r.S;
     if (a.grad_out) {
@@ -303,6 +334,15 @@ __global__ void __launch_bounds__(512) k_score(const AlignArgs a, int L) {
 
 size_t table_bytes(int Lb) { return (size_t)tab_base(Lb + 1, Lb) * sizeof(float4); }
 
+template <int G, int NT>
+int launch_align_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
+  BH_CUDA_TRY(cudaFuncSetAttribute(k_align<G, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BH_CUDA_TRY(cudaFuncSetAttribute(k_align<G, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  k_align<G, NT><<<a.B, NT, smem, stream>>>(a);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
 template <int G>
 int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stream) {
   const int threads = round_up(a.S * G, 32);
@@ -311,13 +351,22 @@ int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stre
   if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
   if (score_only) {
     BH_CUDA_TRY(cudaFuncSetAttribute(k_score<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BH_CUDA_TRY(cudaFuncSetAttribute(k_score<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     k_score<G><<<a.B, threads, smem, stream>>>(a, L);
-  } else {
-    BH_CUDA_TRY(cudaFuncSetAttribute(k_align<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_align<G><<<a.B, threads, smem, stream>>>(a);
+    BH_CHECK_LAUNCH();
+    return BH_OK;
   }
-  BH_CHECK_LAUNCH();
-  return BH_OK;
+  switch (threads) {
+    case 32: return launch_align_nt<G, 32>(a, smem, stream);
+    case 64: return launch_align_nt<G, 64>(a, smem, stream);
+    case 96:
+    case 128: return launch_align_nt<G, 128>(a, smem, stream);
+    case 160:
+    case 192:
+    case 224:
+    case 256: return launch_align_nt<G, 256>(a, smem, stream);
+    default: return launch_align_nt<G, 512>(a, smem, stream);
+  }
 }
 
 int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t stream) {
@@ -340,32 +389,7 @@ int default_group(int S) {
 
 }  // namespace
 
-int align_init_constants() {
-  static std::mutex mu;
-  static bool done[128] = {};
-  int dev = 0;
-  BH_CUDA_TRY(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(mu);
-  if (dev < 128 && done[dev]) return BH_OK;
-  float4 lc[kMaxL + 2];
-  for (int l = 0; l < kMaxL + 2; ++l) {
-    if (l < 2) {
-      lc[l] = make_float4((float)(l * (2 * l - 1)), 0.f, 0.f, 0.f);
-    } else {
-      lc[l] = make_float4((float)(l * (2 * l - 1)), (float)((2.0 * l - 1.0) / (l - 1.0)), (float)((double)l / (l - 1.0)),
-                          0.f);
-    }
-  }
-  static float lb[(kMaxL + 1) * kBinStride];
-  for (int m = 0; m <= kMaxL; ++m)
-    for (int j = 0; j <= 2 * m; ++j)
-      lb[m * kBinStride + j] =
-          (float)(0.5 * (std::lgamma(2.0 * m + 1.0) - std::lgamma(j + 1.0) - std::lgamma(2.0 * m - j + 1.0)) / std::log(2.0));
-  BH_CUDA_TRY(cudaMemcpyToSymbol(c_lconst, lc, sizeof(lc)));
-  BH_CUDA_TRY(cudaMemcpyToSymbol(c_lbin, lb, sizeof(lb)));
-  if (dev < 128) done[dev] = true;
-  return BH_OK;
-}
+int align_init_constants() { return BH_OK; }
 
 }  // namespace bh
 
@@ -395,6 +419,9 @@ extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* s
   a.starts = reinterpret_cast<const float4*>(quats);
   a.S = S;
   a.Lb = L;
+  a.P = p->d_P;
+  a.coef = p->d_coef;
+  a.lbin = p->d_lbin;
   a.score_out = score;
   a.grad_out = grad;
   int G = default_group(S);
@@ -426,6 +453,9 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   for (int i = 0; i < nstages; ++i) a.stages[i] = stages[i];
   a.steps = steps;
   a.Lb = stages[nstages - 1];
+  a.P = p->d_P;
+  a.coef = p->d_coef;
+  a.lbin = p->d_lbin;
   a.quat_out = reinterpret_cast<float4*>(quat_out);
   a.score_out = score_out;
   int G = 0;

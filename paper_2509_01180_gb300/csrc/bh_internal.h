@@ -73,6 +73,9 @@ struct bh_plan {
   __nv_bfloat16* d_Xlo = nullptr;   // [M_cap][V_pad] lo part
   float* d_C = nullptr;             // [M_cap][Nb_pad] real GEMM output
   int* d_err = nullptr;             // device status word written by bounded waits
+  float* d_P = nullptr;             // orbit-table scale P_l(m,n), layout [m][l][n] for l <= Lmax
+  float2* d_coef = nullptr;         // (B_l, g_l) of the rescaled d recursion, same layout
+  float* d_lbin = nullptr;          // 0.5 log2 C(2m, m+n) at [m][m+n], row stride 2 kMaxL + 1
   int gemm_bn = 256;                // N tile of the tensor-core GEMM
   CUtensorMap tm_xhi, tm_xlo, tm_thi, tm_tlo;  // TMA descriptors (BF16 mode)
   int align_group[bh::kMaxL + 1];   // autotuned lanes-per-start by top band (0 = not tuned)

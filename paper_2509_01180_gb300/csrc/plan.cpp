@@ -206,6 +206,9 @@ static void free_plan(bh_plan* p) {
   cudaFree(p->d_Xlo);
   cudaFree(p->d_C);
   cudaFree(p->d_err);
+  cudaFree(p->d_P);
+  cudaFree(p->d_coef);
+  cudaFree(p->d_lbin);
   delete p;
 }
 
@@ -393,6 +396,51 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_Xlo, sizeof(__nv_bfloat16) * x_elems), "cudaMalloc X lo"));
   }
   PLAN_TRY(cuda_ok(cudaMalloc(&p->d_C, sizeof(float) * (size_t)p->M_cap * p->Nb_pad), "cudaMalloc C"));
+  // ---- scale of the rescaled Wigner-d recursion: P_l(m,n) = prod_{j=m+1..l} j(2j-1)/sqrt((j^2-m^2)(j^2-n^2)),
+  //      rows m = 0..Lmax, each [l = m..Lmax][n = -m..m]
+  {
+    std::vector<float> P;
+    for (int m = 0; m <= p->Lmax; ++m) {
+      std::vector<double> cur(2 * m + 1, 1.0);
+      for (int l = m; l <= p->Lmax; ++l) {
+        for (int n = -m; n <= m; ++n) {
+          if (l > m)
+            cur[n + m] *= (double)l * (2.0 * l - 1.0) /
+                          std::sqrt(((double)l * l - (double)m * m) * ((double)l * l - (double)n * n));
+          P.push_back((float)cur[n + m]);
+        }
+      }
+    }
+    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_P, sizeof(float) * P.size()), "cudaMalloc P"));
+    PLAN_TRY(cuda_ok(cudaMemcpy(p->d_P, P.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice), "upload P"));
+    // coefficients of the rescaled recursion e^l = (cos beta - B_l) e^{l-1} - g_l e^{l-2}:
+    //   B_l = m n / (l (l-1)),  g_l = ((l-1)^2 - m^2)((l-1)^2 - n^2) / ((l-1)^2 (2l-1)(2l-3))  (0 at l < 2)
+    std::vector<float2> co;
+    co.reserve(P.size());
+    for (int m = 0; m <= p->Lmax; ++m)
+      for (int l = m; l <= p->Lmax; ++l)
+        for (int n = -m; n <= m; ++n) {
+          double B = 0.0, g = 0.0;
+          if (l >= 2) {
+            const double a = (double)(l - 1) * (l - 1);
+            B = (double)m * n / ((double)l * (l - 1));
+            g = (a - (double)m * m) * (a - (double)n * n) / (a * (2.0 * l - 1.0) * (2.0 * l - 3.0));
+          }
+          co.push_back(make_float2((float)B, (float)g));
+        }
+    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_coef, sizeof(float2) * co.size()), "cudaMalloc coef"));
+    PLAN_TRY(cuda_ok(cudaMemcpy(p->d_coef, co.data(), sizeof(float2) * co.size(), cudaMemcpyHostToDevice), "upload coef"));
+    // 0.5 log2 C(2m, j), j = m + n
+    const int stride = 2 * kMaxL + 1;
+    std::vector<float> lb((size_t)(kMaxL + 1) * stride, 0.f);
+    for (int m = 0; m <= kMaxL; ++m)
+      for (int j = 0; j <= 2 * m; ++j)
+        lb[(size_t)m * stride + j] =
+            (float)(0.5 * (std::lgamma(2.0 * m + 1.0) - std::lgamma(j + 1.0) - std::lgamma(2.0 * m - j + 1.0)) /
+                    std::log(2.0));
+    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_lbin, sizeof(float) * lb.size()), "cudaMalloc lbin"));
+    PLAN_TRY(cuda_ok(cudaMemcpy(p->d_lbin, lb.data(), sizeof(float) * lb.size(), cudaMemcpyHostToDevice), "upload lbin"));
+  }
   const double hv = 2.0 / N;
   PLAN_TRY(upload_table(p, radial, n_r2, angular, vox_r2, colinfo, hv * hv * hv));
   if (p->mode == BH_MODE_BF16_SPLIT) PLAN_TRY(make_tensor_maps(p));

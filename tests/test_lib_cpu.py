@@ -64,3 +64,17 @@ def test_plan_create_without_gpu_fails_cleanly(built):
     with pytest.raises(bh.BHError) as e:
         bh.bh_plan_create(16, 8)
     assert e.value.status in (bh.BH_ERR_CUDA, bh.BH_ERR_UNSUPPORTED)
+
+
+def test_random_starts_are_deterministic_uniform_rotations(built):
+    q = bh.bh_random_starts(2509, 400, 50)
+    assert q.shape == (400, 50, 4)
+    assert np.allclose(np.linalg.norm(q, axis=-1), 1.0, atol=1e-6)
+    assert (q[..., 0] >= 0).all()
+    assert np.array_equal(q, bh.bh_random_starts(2509, 400, 50))
+    # start (b, s) depends only on (seed, b, s): a prefix of a larger batch is the smaller batch
+    assert np.array_equal(bh.bh_random_starts(7, 3, 50), bh.bh_random_starts(7, 5, 50)[:3])
+    # Haar measure: E[q_i^2] = 1/4 for every component, and E[trace R] = 0 (trace R = 4 w^2 - 1)
+    m2 = (q.reshape(-1, 4).astype(np.float64) ** 2).mean(axis=0)
+    assert np.allclose(m2, 0.25, atol=0.01)
+    assert abs(np.mean(4 * q[..., 0].astype(np.float64) ** 2 - 1)) < 0.02
