@@ -52,15 +52,22 @@ def orbit_steps(L: int) -> int:
     return sum((2 * m + 1) * (L - m + 1) for m in range(L + 1))
 
 
-# flop accounting of one orbit-step of the FP32 kernel (recursion coefficients 12, d and d' recursion 11,
-# eight accumulating FMAs 16): 39 flop
-FLOP_PER_ORBIT_STEP = 39
+# FP32 flop accounting of the alignment kernel (FMA = 2 flop), per score+gradient evaluation at band L:
+#   each orbit-step (one l of one (m,n) orbit): t 2, g 4, e-recursion 3, e'-recursion 5, 8 accumulating
+#   FMAs 16 -> 30 flop;  each orbit ((L+1)^2 of them): seed and derivative seed 10, phases and the four
+#   sums 36 -> 46 flop.
+FLOP_PER_ORBIT_STEP = 30
+FLOP_PER_ORBIT = 46
+
+
+def eval_flops(L: int) -> int:
+    return FLOP_PER_ORBIT_STEP * orbit_steps(L) + FLOP_PER_ORBIT * (L + 1) ** 2
 
 
 def align_flops(w) -> float:
     """FP32 flop of bh_align_batch on the workload: every start runs (1 + steps) evaluations per stage."""
-    per_start = sum((1 + w.steps) * orbit_steps(L) for L in w.stages)
-    return float(w.B) * w.S * per_start * FLOP_PER_ORBIT_STEP
+    per_start = sum((1 + w.steps) * eval_flops(L) for L in w.stages)
+    return float(w.B) * w.S * per_start
 
 
 class ClockSampler:
@@ -78,7 +85,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -231,6 +238,7 @@ def run_ours(args, rank, world, device):
         t0 = time.perf_counter()
         plan = bh.bh_plan_create(w.N, w.Lmax, w.lam_max, forms[name], max_batch=min(B, 4096))
         plan_s = time.perf_counter() - t0
+        tune = bh.bh_autotune(plan, B, w.S, w.stages, w.steps)  # picks kernel variants (untimed setup)
         tmpl = bh.bh_expand(plan, tvol)[0].contiguous()
         coeffs = torch.empty((B, plan.Nb, 2), dtype=torch.float32, device=device)
         quat = torch.empty((B, 4), dtype=torch.float32, device=device)
@@ -293,7 +301,7 @@ def run_ours(args, rank, world, device):
             tt = torch.tensor([e2e_ms], device=device)
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
             e2e_ms = float(tt[0])
-        results[name] = {"plan_s": plan_s, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
+        results[name] = {"plan_s": plan_s, "tune": tune, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
                          "clocks": clk.summary(), "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V,
                          "h2d": int(hv.numel() * 4), "d2h": int(hq.numel() * 4 + hs.numel() * 4)}
         plan.destroy()
@@ -310,7 +318,7 @@ def angle_deg(q1, q2):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batch32")
@@ -378,6 +386,8 @@ def main():
                        "expansion": "tcgen05 BF16 hi/lo split, FP32 accumulate" if main_form == "bf16split"
                        else "FP32 FFMA", "ascent": "FP32", "l2": "flushed between timed steps (256 MB write)",
                        "template": "expanded once before timing (resident)",
+                       "autotuned": {"align_lanes_per_start": r["tune"]["align_group"],
+                                     "gemm_n_tile": r["tune"]["gemm_bn"]},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "breakdown_ms_per_step": {"expand": per_step_exp, "align": per_step_aln, "plan_create_s": r["plan_s"]},
             "roofline": roof,

@@ -164,8 +164,10 @@ typedef struct {
   int n_templates;        /* rows in `tmpl` when tmpl_index is given */
   float* start_quat_out;  /* device, B * S * 4 floats or NULL: final rotation of every start */
   float* start_score_out; /* device, B * S floats or NULL: final score of every start */
-  int refine_fp64;        /* 1: re-score every start's final rotation in FP64 at the last band and
-                             select on those scores (score_out then holds the FP64 score) */
+  int refine_fp64;        /* K in 0..64: after the FP32 ascent, re-score the K best starts (by FP32
+                             score) at the last band with the d-recursion, seeds, phases and sums in
+                             FP64 and select among them on the FP64 score (score_out then holds it,
+                             rounded to float).  Needs start_quat_out and start_score_out.  0 = off */
 } bh_align_opts;
 
 /*
@@ -188,6 +190,22 @@ typedef struct {
 int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int B,
                    const float* starts, int S, const int* stages, int nstages, int steps,
                    float* quat_out, float* score_out, const bh_align_opts* opts, void* stream);
+
+/* ------------------------------------------------------------------ autotuning */
+typedef struct {
+  int align_group;  /* lanes per start chosen for (band stages[nstages-1], S) */
+  float align_ms;   /* its time for B subtomograms */
+  int gemm_bn;      /* N tile of the tensor-core expansion GEMM (BF16 mode; 0 in FP32 mode) */
+  float expand_ms;  /* bh_expand time for B volumes with that tile */
+} bh_tune_result;
+
+/*
+ * Time the variants of the two hot kernels on synthetic data of this shape (B subtomograms, S starts,
+ * the given marching schedule) and keep the fastest in the plan: bh_align_batch with group = 0 then
+ * uses the chosen lanes-per-start for this (top band, S), and bh_expand the chosen GEMM N tile.
+ * Allocates and frees its own temporary device buffers; synchronous.  `out` may be NULL.
+ */
+int bh_autotune(bh_plan* plan, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out);
 
 /* ------------------------------------------------------------------ random starts */
 /*

@@ -22,7 +22,7 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
-           "bh_align_batch", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_align_batch", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
@@ -186,7 +186,8 @@ def bh_score_grad(plan: Plan, tmpl, sub, quats, L: int, with_grad: bool = True, 
 
 # ------------------------------------------------------------------ alignment
 def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
-                   n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None):
+                   n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None,
+                   refine_fp64: int = 0):
     """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
     import torch
     B, S = starts.shape[0], starts.shape[1]
@@ -199,8 +200,9 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
     o = AlignOpts()
     o.group = group
+    o.refine_fp64 = refine_fp64
     sq = ss = None
-    if per_start:
+    if per_start or refine_fp64:
         sq = torch.empty((B, S, 4), dtype=torch.float32, device=dev)
         ss = torch.empty((B, S), dtype=torch.float32, device=dev)
         o.start_quat_out, o.start_score_out = _ptr(sq), _ptr(ss)
@@ -223,6 +225,19 @@ def bh_random_starts(seed: int, B: int, S: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ serving
+class TuneResult(ctypes.Structure):
+    _fields_ = [("align_group", ctypes.c_int), ("align_ms", ctypes.c_float), ("gemm_bn", ctypes.c_int),
+                ("expand_ms", ctypes.c_float)]
+
+
+def bh_autotune(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
+    """Time the kernel variants for this shape and keep the fastest in the plan."""
+    st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
+    r = TuneResult()
+    _check(lib().bh_autotune(plan.handle, B, S, st, len(stages), steps, ctypes.byref(r)), "bh_autotune")
+    return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+
 class ServeOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int)]
@@ -244,6 +259,7 @@ def _serve_sigs(L):
     if getattr(L, "_serve_ready", False):
         return
     L.bh_random_starts.argtypes = [ctypes.c_uint64, i, i, vp]
+    L.bh_autotune.argtypes = [vp, i, i, vp, i, i, ctypes.POINTER(TuneResult)]
     L.bh_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeOpts)]
     L.bh_serve_add_template.argtypes = [vp, i, vp, ctypes.POINTER(i)]
     L.bh_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -252,7 +268,7 @@ def _serve_sigs(L):
     L.bh_serve_pause.argtypes = [vp, i]
     L.bh_serve_stats.argtypes = [vp, ctypes.POINTER(ServeCounters)]
     L.bh_serve_destroy.argtypes = [vp]
-    for n in ("bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
+    for n in ("bh_random_starts", "bh_autotune", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
               "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"):
         getattr(L, n).restype = i
     L._serve_ready = True

@@ -41,6 +41,10 @@ namespace {
 
 constexpr int kBinStride = 2 * kMaxL + 1;
 
+// Per-band constants of the rescaled recursion, read with a warp-uniform index (every lane of a warp
+// steps through the same l): l >= 2: (1/(l(l-1)), 1/((l-1)^2 (2l-1)(2l-3)), (l-1)^2, 0); zero below.
+__constant__ float4 c_ecoef[kMaxL + 2];
+
 constexpr int kMaxStages = 8;
 constexpr int kMaxThreads = 512;  // threads per CTA (S * G rounded up to a warp)
 
@@ -65,6 +69,7 @@ struct AlignArgs {
   float4* start_quat_out;
   float* start_score_out;
   float* grad_out;  // score kernel: [B][S][3]
+  double* score64_out;  // refine kernel: [B] FP64 score of the selected start (may be NULL)
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -151,7 +156,7 @@ __device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, flo
   for (int m = 0; m <= L; ++m) {
     const int w = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
-    const float2* crow = coef + tab_base(m, Lmax);
+    const float fm2 = (float)(m * m);
     float2 U = Uq, W = Wrow;
     for (int n = qg - m; n <= m; n += G) {
       // seed at l = m: d = sg 2^lb c^(m+n) s^(m-n), c = cos(beta/2), s = sin(beta/2) (both clamped to
@@ -163,17 +168,19 @@ __device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, flo
       d = ((m - n) & 1) ? -d : d;
       const float dp = 0.5f * d * (fd * rcs - fa * rsc);
       const float4* ep = rowp + (n + m);
-      const float2* kp = crow + (n + m);
       float4 xv = *ep;
       float a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
       float b1r = dp * xv.x, b1i = dp * xv.y, b2r = dp * xv.z, b2i = dp * xv.w;
       float e1 = d, e2 = 0.f, p1 = dp, p2 = 0.f;
+      const float mn = (float)(m * n), fn2 = (float)(n * n);
       int l = m + 1;
+      // one step: t = cos(beta) - m n / (l(l-1)),  g = ((l-1)^2 - m^2)((l-1)^2 - n^2) / ((l-1)^2 (2l-1)(2l-3))
 #define BH_ORBIT_STEP(E_NEW, P_NEW, E1, E2, P1, P2, K, X)                   \
   {                                                                        \
-    const float t_ = xb - (K).x;                                           \
-    E_NEW = fmaf(t_, E1, -(K).y * E2);                                     \
-    P_NEW = fmaf(t_, P1, -fmaf(sinb, E1, (K).y * P2));                     \
+    const float t_ = fmaf(-mn, (K).x, xb);                                 \
+    const float g_ = ((K).z - fm2) * ((K).z - fn2) * (K).y;                \
+    E_NEW = fmaf(t_, E1, -g_ * E2);                                        \
+    P_NEW = fmaf(t_, P1, -fmaf(sinb, E1, g_ * P2));                        \
     a1r = fmaf(E_NEW, (X).x, a1r);                                         \
     a1i = fmaf(E_NEW, (X).y, a1i);                                         \
     a2r = fmaf(E_NEW, (X).z, a2r);                                         \
@@ -185,12 +192,10 @@ __device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, flo
   }
       for (; l + 1 <= L; l += 2) {
         ep += w;
-        kp += w;
-        const float2 k0 = __ldg(kp);
+        const float4 k0 = c_ecoef[l];
         const float4 x0 = *ep;
         ep += w;
-        kp += w;
-        const float2 k1 = __ldg(kp);
+        const float4 k1 = c_ecoef[l + 1];
         const float4 x1 = *ep;
         float ea, pa, eb, pb;
         BH_ORBIT_STEP(ea, pa, e1, e2, p1, p2, k0, x0);
@@ -202,8 +207,7 @@ __device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, flo
       }
       if (l <= L) {
         ep += w;
-        kp += w;
-        const float2 k0 = __ldg(kp);
+        const float4 k0 = c_ecoef[l];
         const float4 x0 = *ep;
         float ea, pa;
         BH_ORBIT_STEP(ea, pa, e1, e2, p1, p2, k0, x0);
@@ -332,6 +336,117 @@ __global__ void __launch_bounds__(512, 1) k_score(const AlignArgs a, int L) {
   }
 }
 
+// ---------------------------------------------------------------------------- FP64 re-scoring
+// The same evaluation with the d-recursion, its coefficients, the seeds, the phases and every sum in
+// FP64 (the shared-memory table stays FP32: P_l xi^l rounded once per entry).  Used to re-score the
+// best starts at the last band and select among them in FP64.
+struct Cx64 {
+  double x, y;
+};
+__device__ __forceinline__ Cx64 cm64(Cx64 a, Cx64 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ Cx64 cj64(Cx64 a) { return {a.x, -a.y}; }
+__device__ __forceinline__ Cx64 cp64(Cx64 a, int k) {
+  Cx64 r{1.0, 0.0};
+  for (int i = 0; i < k; ++i) r = cm64(r, a);
+  return r;
+}
+
+template <int G>
+__device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L, float4 qf, int qg,
+                                   const double2* __restrict__ coef, const double* __restrict__ lbin, int Lmax) {
+  double w = qf.x, x = qf.y, y = qf.z, z = qf.w;
+  const double nq = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+  w *= nq; x *= nq; y *= nq; z *= nq;
+  const double cb = sqrt(w * w + z * z), sb = sqrt(x * x + y * y);
+  const Cx64 es = cb > 0.0 ? Cx64{w / cb, z / cb} : Cx64{1.0, 0.0};
+  const Cx64 ed = sb > 0.0 ? Cx64{y / sb, -x / sb} : Cx64{1.0, 0.0};
+  const double xb = (cb - sb) * (cb + sb);
+  const double lcc = log2(fmax(cb, 1e-300)), lss = log2(fmax(sb, 1e-300));
+  const Cx64 Es = cj64(es), EsG = cp64(Es, G), edG = cp64(ed, G), Ed = cj64(ed), Ed2 = cm64(Ed, Ed);
+  const Cx64 Uq = cp64(Es, qg);
+  Cx64 Wrow = cp64(ed, qg);
+  double S = 0.0;
+  for (int m = 0; m <= L; ++m) {
+    const int w2 = 2 * m + 1;
+    const float4* rowp = tab + tab_base(m, Lb);
+    const double2* crow = coef + tab_base(m, Lmax);
+    Cx64 U = Uq, W = Wrow;
+    for (int n = qg - m; n <= m; n += G) {
+      double d = exp2(lbin[m * kBinStride + m + n] + (double)(m + n) * lcc + (double)(m - n) * lss);
+      d = ((m - n) & 1) ? -d : d;
+      const float4* ep = rowp + (n + m);
+      const double2* kp = crow + (n + m);
+      float4 xv = *ep;
+      double a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
+      double e1 = d, e2 = 0.0;
+      for (int l = m + 1; l <= L; ++l) {
+        ep += w2;
+        kp += w2;
+        const double2 k = __ldg(kp);
+        const double en = fma(xb - k.x, e1, -k.y * e2);
+        e2 = e1;
+        e1 = en;
+        xv = *ep;
+        a1r = fma(en, (double)xv.x, a1r);
+        a1i = fma(en, (double)xv.y, a1i);
+        a2r = fma(en, (double)xv.z, a2r);
+        a2i = fma(en, (double)xv.w, a2i);
+      }
+      const Cx64 P1 = cm64(U, W), P2 = cm64(U, cj64(W));
+      S += (P1.x * a1r - P1.y * a1i) + (P2.x * a2r - P2.y * a2i);
+      U = cm64(U, EsG);
+      W = cm64(W, edG);
+    }
+    Wrow = cm64(Wrow, Ed2);
+  }
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+  return S;
+}
+
+constexpr int kMaxRefine = 64;
+
+// Re-score the K best starts (by their FP32 final score) of every subtomogram in FP64 at band L and
+// select among them on the FP64 score (exact ties: lowest start index).  blockDim = roundup(K G, 32).
+template <int G>
+__global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, int K, const double2* coef64,
+                                                     const double* lbin64) {
+  extern __shared__ float4 smem_tab[];
+  __shared__ int top[kMaxRefine];
+  __shared__ double s64[kMaxRefine];
+  const int p = blockIdx.x;
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
+  if (threadIdx.x == 0) {
+    const float* sc = a.start_score_out + (size_t)p * a.S;
+    for (int k = 0; k < K; ++k) {
+      int best = -1;
+      for (int j = 0; j < a.S; ++j) {
+        bool taken = false;
+        for (int i = 0; i < k; ++i) taken |= (top[i] == j);
+        if (!taken && (best < 0 || sc[j] > sc[best])) best = j;
+      }
+      top[k] = best;
+    }
+  }
+  __syncthreads();
+  const int s = threadIdx.x / G, qg = threadIdx.x % G;
+  const bool active = s < K;
+  const int idx = top[active ? s : s % K];
+  const float4 q = a.start_quat_out[(size_t)p * a.S + idx];
+  const double S = score_rotation64<G>(smem_tab, a.Lb, L, q, qg, coef64, lbin64, a.lay.Lmax);
+  if (active && qg == 0) s64[s] = S;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int k = 1; k < K; ++k)
+      if (s64[k] > s64[best] || (s64[k] == s64[best] && top[k] < top[best])) best = k;
+    a.quat_out[p] = a.start_quat_out[(size_t)p * a.S + top[best]];
+    a.score_out[p] = (float)s64[best];
+    if (a.score64_out) a.score64_out[p] = s64[best];
+  }
+}
+
 size_t table_bytes(int Lb) { return (size_t)tab_base(Lb + 1, Lb) * sizeof(float4); }
 
 template <int G, int NT>
@@ -380,16 +495,59 @@ int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t
   }
 }
 
-// Default lanes per start: aim at >= 128 threads per CTA, capped by 1024 threads and 16 lanes.
+template <int G>
+int launch_refine_g(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
+  const int threads = round_up(K * G, 32);
+  const size_t smem = table_bytes(a.Lb);
+  BH_CUDA_TRY(cudaFuncSetAttribute(k_refine64<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BH_CUDA_TRY(cudaFuncSetAttribute(k_refine64<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  k_refine64<G><<<a.B, threads, smem, stream>>>(a, L, K, p->d_coef64, p->d_lbin64);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+int launch_refine(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
+  int G = 1;
+  while (G < 16 && K * G < 128 && K * G * 2 <= kMaxThreads) G *= 2;
+  switch (G) {
+    case 1: return launch_refine_g<1>(a, L, K, p, stream);
+    case 2: return launch_refine_g<2>(a, L, K, p, stream);
+    case 4: return launch_refine_g<4>(a, L, K, p, stream);
+    case 8: return launch_refine_g<8>(a, L, K, p, stream);
+    default: return launch_refine_g<16>(a, L, K, p, stream);
+  }
+}
+
+// Default lanes per start (before autotuning): aim at 64 threads per CTA.
 int default_group(int S) {
   int G = 1;
-  while (G < 16 && S * G < 128 && S * G * 2 <= kMaxThreads) G *= 2;
+  while (G < 16 && S * G < 64 && S * G * 2 <= kMaxThreads) G *= 2;
   return G;
 }
 
 }  // namespace
 
-int align_init_constants() { return BH_OK; }
+int align_init_constants() {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  BH_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 128 && done[dev]) return BH_OK;
+  float4 ec[kMaxL + 2];
+  for (int l = 0; l < kMaxL + 2; ++l) {
+    if (l < 2) {
+      ec[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      const double a = (double)(l - 1) * (l - 1);
+      ec[l] = make_float4((float)(1.0 / ((double)l * (l - 1))), (float)(1.0 / (a * (2.0 * l - 1.0) * (2.0 * l - 3.0))),
+                          (float)a, 0.f);
+    }
+  }
+  BH_CUDA_TRY(cudaMemcpyToSymbol(c_ecoef, ec, sizeof(ec)));
+  if (dev >= 0 && dev < 128) done[dev] = true;
+  return BH_OK;
+}
 
 }  // namespace bh
 
@@ -468,9 +626,121 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     a.start_quat_out = reinterpret_cast<float4*>(opts->start_quat_out);
     a.start_score_out = opts->start_score_out;
     G = opts->group;
-    if (opts->refine_fp64) return fail(BH_ERR_UNSUPPORTED, "refine_fp64 is not available in this build");
+    if (opts->refine_fp64 < 0 || opts->refine_fp64 > kMaxRefine)
+      return fail(BH_ERR_ARG, "refine_fp64=%d outside 0..%d", opts->refine_fp64, kMaxRefine);
+    if (opts->refine_fp64 > 0 && (!opts->start_quat_out || !opts->start_score_out))
+      return fail(BH_ERR_ARG, "refine_fp64 needs start_quat_out and start_score_out");
   }
-  if (G == 0) G = p->align_group[a.Lb] > 0 ? p->align_group[a.Lb] : default_group(S);
+  if (G == 0) {
+    auto it = p->align_group.find({a.Lb, S});
+    G = (it != p->align_group.end()) ? it->second : default_group(S);
+  }
   if (round_up(S * G, 32) > kMaxThreads) return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
-  return launch_align(a, G, false, 0, static_cast<cudaStream_t>(stream));
+  st = launch_align(a, G, false, 0, static_cast<cudaStream_t>(stream));
+  if (st != BH_OK || !opts || opts->refine_fp64 == 0) return st;
+  return launch_refine(a, a.Lb, std::min(opts->refine_fp64, S), p, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 1 || B > (1 << 20)) return fail(BH_ERR_ARG, "B=%d", B);
+  if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d", S);
+  if (!stages || nstages < 1 || nstages > kMaxStages) return fail(BH_ERR_ARG, "nstages=%d", nstages);
+  const int Lb = stages[nstages - 1];
+  if (Lb < 1 || Lb > p->Lmax) return fail(BH_ERR_ARG, "band %d", Lb);
+  cudaStream_t st;
+  BH_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  BH_CUDA_TRY(cudaEventCreate(&e0));
+  BH_CUDA_TRY(cudaEventCreate(&e1));
+  float *coef = nullptr, *tmpl = nullptr, *starts = nullptr, *quat = nullptr, *score = nullptr, *vols = nullptr;
+  const size_t N3 = (size_t)p->N * p->N * p->N;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(coef); cudaFree(tmpl); cudaFree(starts); cudaFree(quat); cudaFree(score); cudaFree(vols);
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaStreamDestroy(st);
+  };
+#define AT_TRY(call)                                                                                      \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess) {                                                                              \
+      cleanup();                                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA, "%s: %s", #call,            \
+                  cudaGetErrorString(e_));                                                                \
+    }                                                                                                     \
+  } while (0)
+  AT_TRY(cudaMalloc(&coef, (size_t)B * p->Nb * 8));
+  AT_TRY(cudaMalloc(&tmpl, (size_t)p->Nb * 8));
+  AT_TRY(cudaMalloc(&starts, (size_t)B * S * 16));
+  AT_TRY(cudaMalloc(&quat, (size_t)B * 16));
+  AT_TRY(cudaMalloc(&score, (size_t)B * 4));
+  // value-independent timing: every byte 0x3C (float ~0.0115, never denormal)
+  AT_TRY(cudaMemsetAsync(coef, 0x3C, (size_t)B * p->Nb * 8, st));
+  AT_TRY(cudaMemsetAsync(tmpl, 0x3C, (size_t)p->Nb * 8, st));
+  AT_TRY(cudaMemsetAsync(starts, 0x3C, (size_t)B * S * 16, st));
+  int best_g = 0;
+  float best_ms = 1e30f;
+  for (int G : {1, 2, 4, 8, 16}) {
+    if (round_up(S * G, 32) > kMaxThreads) continue;
+    bh_align_opts o{};
+    o.group = G;
+    int rc = BH_OK;
+    for (int it = 0; it < 2 && rc == BH_OK; ++it)
+      rc = bh_align_batch(p, tmpl, coef, B, starts, S, stages, nstages, steps, quat, score, &o, st);
+    if (rc != BH_OK) continue;
+    AT_TRY(cudaEventRecord(e0, st));
+    for (int it = 0; it < 3; ++it) bh_align_batch(p, tmpl, coef, B, starts, S, stages, nstages, steps, quat, score, &o, st);
+    AT_TRY(cudaEventRecord(e1, st));
+    AT_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AT_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    ms /= 3.f;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_g = G;
+    }
+  }
+  if (best_g == 0) {
+    cleanup();
+    return fail(BH_ERR_UNSUPPORTED, "no alignment variant runs for S=%d band %d", S, Lb);
+  }
+  p->align_group[{Lb, S}] = best_g;
+  int best_bn = 0;
+  float best_ems = 0.f;
+  if (p->mode == BH_MODE_BF16_SPLIT) {
+    AT_TRY(cudaMalloc(&vols, (size_t)B * N3 * 4));
+    AT_TRY(cudaMemsetAsync(vols, 0x3C, (size_t)B * N3 * 4, st));
+    best_ems = 1e30f;
+    for (int bn : {256, 128}) {
+      int rc = set_gemm_bn(p, bn);
+      for (int it = 0; it < 2 && rc == BH_OK; ++it) rc = bh_expand(p, vols, B, coef, st);
+      if (rc != BH_OK) continue;
+      AT_TRY(cudaEventRecord(e0, st));
+      for (int it = 0; it < 3; ++it) bh_expand(p, vols, B, coef, st);
+      AT_TRY(cudaEventRecord(e1, st));
+      AT_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      AT_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      ms /= 3.f;
+      if (ms < best_ems) {
+        best_ems = ms;
+        best_bn = bn;
+      }
+    }
+    int rc = set_gemm_bn(p, best_bn ? best_bn : 256);
+    if (rc != BH_OK) {
+      cleanup();
+      return rc;
+    }
+  }
+#undef AT_TRY
+  cleanup();
+  if (out) {
+    out->align_group = best_g;
+    out->align_ms = best_ms;
+    out->gemm_bn = best_bn;
+    out->expand_ms = best_ems;
+  }
+  return BH_OK;
 }

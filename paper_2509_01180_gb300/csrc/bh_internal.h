@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -76,9 +77,11 @@ struct bh_plan {
   float* d_P = nullptr;             // orbit-table scale P_l(m,n), layout [m][l][n] for l <= Lmax
   float2* d_coef = nullptr;         // (B_l, g_l) of the rescaled d recursion, same layout
   float* d_lbin = nullptr;          // 0.5 log2 C(2m, m+n) at [m][m+n], row stride 2 kMaxL + 1
+  double2* d_coef64 = nullptr;      // FP64 copies of the two tables above (FP64 re-scoring)
+  double* d_lbin64 = nullptr;
   int gemm_bn = 256;                // N tile of the tensor-core GEMM
   CUtensorMap tm_xhi, tm_xlo, tm_thi, tm_tlo;  // TMA descriptors (BF16 mode)
-  int align_group[bh::kMaxL + 1];   // autotuned lanes-per-start by top band (0 = not tuned)
+  std::map<std::pair<int, int>, int> align_group;  // autotuned lanes-per-start by (top band, S)
 };
 
 namespace bh {
@@ -86,6 +89,7 @@ namespace bh {
 int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const std::vector<double>& angular,
                  const std::vector<int>& vox_r2, const std::vector<int2>& colinfo, double h3);
 int make_tensor_maps(bh_plan* p);
+int set_gemm_bn(bh_plan* p, int bn);
 int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scratch_x, float* scratch_c, int rows_cap,
                 cudaStream_t stream);
 // align.cu

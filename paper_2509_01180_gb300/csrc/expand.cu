@@ -437,6 +437,16 @@ int make_tensor_maps(bh_plan* p) {
   return BH_OK;
 }
 
+int set_gemm_bn(bh_plan* p, int bn) {
+  if (bn != 128 && bn != 256) return fail(BH_ERR_ARG, "GEMM N tile %d not in {128, 256}", bn);
+  if (p->mode != BH_MODE_BF16_SPLIT || p->gemm_bn == bn) {
+    p->gemm_bn = bn;
+    return BH_OK;
+  }
+  p->gemm_bn = bn;
+  return make_tensor_maps(p);
+}
+
 static int launch_gemm(bh_plan* p, int Mp, cudaStream_t stream) {
   if (p->mode == BH_MODE_FP32) {
     dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM);

@@ -209,6 +209,8 @@ static void free_plan(bh_plan* p) {
   cudaFree(p->d_P);
   cudaFree(p->d_coef);
   cudaFree(p->d_lbin);
+  cudaFree(p->d_coef64);
+  cudaFree(p->d_lbin64);
   delete p;
 }
 
@@ -241,7 +243,6 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   p->mode = o->mode;
   p->max_batch = max_batch;
   p->lam_max = lam_max;
-  for (int l = 0; l <= kMaxL; ++l) p->align_group[l] = 0;
 
   // ---- index set (FP64 roots and constants)
   compute_roots(p->Lmax, lam_max, p->K, p->lam, p->cst);
@@ -416,7 +417,9 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     // coefficients of the rescaled recursion e^l = (cos beta - B_l) e^{l-1} - g_l e^{l-2}:
     //   B_l = m n / (l (l-1)),  g_l = ((l-1)^2 - m^2)((l-1)^2 - n^2) / ((l-1)^2 (2l-1)(2l-3))  (0 at l < 2)
     std::vector<float2> co;
+    std::vector<double2> co64;
     co.reserve(P.size());
+    co64.reserve(P.size());
     for (int m = 0; m <= p->Lmax; ++m)
       for (int l = m; l <= p->Lmax; ++l)
         for (int n = -m; n <= m; ++n) {
@@ -427,19 +430,28 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
             g = (a - (double)m * m) * (a - (double)n * n) / (a * (2.0 * l - 1.0) * (2.0 * l - 3.0));
           }
           co.push_back(make_float2((float)B, (float)g));
+          co64.push_back(make_double2(B, g));
         }
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_coef, sizeof(float2) * co.size()), "cudaMalloc coef"));
     PLAN_TRY(cuda_ok(cudaMemcpy(p->d_coef, co.data(), sizeof(float2) * co.size(), cudaMemcpyHostToDevice), "upload coef"));
     // 0.5 log2 C(2m, j), j = m + n
     const int stride = 2 * kMaxL + 1;
     std::vector<float> lb((size_t)(kMaxL + 1) * stride, 0.f);
+    std::vector<double> lb64((size_t)(kMaxL + 1) * stride, 0.0);
     for (int m = 0; m <= kMaxL; ++m)
-      for (int j = 0; j <= 2 * m; ++j)
-        lb[(size_t)m * stride + j] =
-            (float)(0.5 * (std::lgamma(2.0 * m + 1.0) - std::lgamma(j + 1.0) - std::lgamma(2.0 * m - j + 1.0)) /
-                    std::log(2.0));
+      for (int j = 0; j <= 2 * m; ++j) {
+        lb64[(size_t)m * stride + j] =
+            0.5 * (std::lgamma(2.0 * m + 1.0) - std::lgamma(j + 1.0) - std::lgamma(2.0 * m - j + 1.0)) / std::log(2.0);
+        lb[(size_t)m * stride + j] = (float)lb64[(size_t)m * stride + j];
+      }
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_lbin, sizeof(float) * lb.size()), "cudaMalloc lbin"));
     PLAN_TRY(cuda_ok(cudaMemcpy(p->d_lbin, lb.data(), sizeof(float) * lb.size(), cudaMemcpyHostToDevice), "upload lbin"));
+    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_coef64, sizeof(double2) * co64.size()), "cudaMalloc coef64"));
+    PLAN_TRY(cuda_ok(cudaMemcpy(p->d_coef64, co64.data(), sizeof(double2) * co64.size(), cudaMemcpyHostToDevice),
+                     "upload coef64"));
+    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_lbin64, sizeof(double) * lb64.size()), "cudaMalloc lbin64"));
+    PLAN_TRY(cuda_ok(cudaMemcpy(p->d_lbin64, lb64.data(), sizeof(double) * lb64.size(), cudaMemcpyHostToDevice),
+                     "upload lbin64"));
   }
   const double hv = 2.0 / N;
   PLAN_TRY(upload_table(p, radial, n_r2, angular, vox_r2, colinfo, hv * hv * hv));

@@ -75,7 +75,7 @@ def test_served_result_equals_batch_api(srv):
 def test_budget_admission_rejects_requests_that_never_fit():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    s = bh.bh_serve_create(hbm_budget_bytes=1 << 20, max_batch=4096)
+    s = bh.bh_serve_create(hbm_budget_bytes=4 << 20, max_batch=4096)
     tpl = synth.blob_template(synth.rng_for(9, 1), 10, 1.2, 6.0)
     tid = s.add_template(synth.render(16, tpl).astype(np.float32))
     with pytest.raises(bh.BHError) as e:
