@@ -222,8 +222,9 @@ def run_ours(args, rank, world, device):
 
     from paper_2509_01180_gb300 import bh, synth
 
-    count = args.count
-    w = synth.make_workload(args.workload, count=count, first=rank * (count or 0))
+    from paper_2509_01180_gb300 import replicas
+    count = args.count or synth.CONFIGS[args.workload][-1]
+    w = synth.make_workload(args.workload, count=count, first=replicas.shard_first(rank, count))
     B = w.B
     forms = {"bf16split": bh.BH_MODE_BF16_SPLIT, "fp32": bh.BH_MODE_FP32}
     order = [args.form] if args.form != "both" else ["bf16split", "fp32"]
@@ -253,8 +254,7 @@ def run_ours(args, rank, world, device):
             step()
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
         torch.cuda.synchronize(device)
-        if dist:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize(device)
         with ClockSampler(device.index if device.index is not None else 0) as clk:
             for k in range(args.steps):
@@ -266,15 +266,11 @@ def run_ours(args, rank, world, device):
                 ev[k][2].record(stream)
                 flush.zero_()  # evict L2 between timed steps (not timed)
             torch.cuda.synchronize(device)
-        if dist:
-            torch.distributed.barrier()
+        replicas.barrier()
         t_exp = sum(e[0].elapsed_time(e[1]) for e in ev)
         t_aln = sum(e[1].elapsed_time(e[2]) for e in ev)
         t_tot = t_exp + t_aln
-        if dist:
-            tt = torch.tensor([t_tot, t_exp, t_aln], device=device)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t_tot, t_exp, t_aln = [float(x) for x in tt]
+        t_tot, t_exp, t_aln = replicas.max_over_ranks([t_tot, t_exp, t_aln], device)
         q_res = quat.cpu().numpy().astype(np.float64)
 
         # end to end through the public API: pinned host volumes in, rotations and scores out
@@ -297,10 +293,7 @@ def run_ours(args, rank, world, device):
             if k >= args.warmup:
                 e2e_ms += e0.elapsed_time(e1)
             flush.zero_()
-        if dist:
-            tt = torch.tensor([e2e_ms], device=device)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(tt[0])
+        e2e_ms = replicas.max_over_ranks([e2e_ms], device)[0]
         results[name] = {"plan_s": plan_s, "tune": tune, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
                          "clocks": clk.summary(), "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V,
                          "h2d": int(hv.numel() * 4), "d2h": int(hq.numel() * 4 + hs.numel() * 4)}
