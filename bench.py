@@ -302,6 +302,63 @@ def run_ours(args, rank, world, device):
     return w, results
 
 
+def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
+    """Continuous-batching server under a Poisson stream of requests (mean `rate` req/s for `seconds`):
+    1-512 subtomograms per request (log-uniform), box edge uniform over {24, 32, 48, 64}, one of 8 resident
+    templates (2 per box), 16 starts, bands N/8 -> N/4 -> N/2, 30 steps; noise (SNR 0.1) and a +-60 deg
+    wedge as in the batch workload.  Volumes come from a pool of 64 distinct phantoms per box (tiled to
+    512) so that host memory stays bounded; the arithmetic per subtomogram is the same."""
+    import numpy as np
+
+    from paper_2509_01180_gb300 import bh, synth
+    rng = np.random.default_rng(seed)
+    boxes = [24, 32, 48, 64]
+    t_setup = time.perf_counter()
+    srv = bh.bh_serve_create(hbm_budget_bytes=48 << 30, max_inflight=4, max_batch=2048,
+                             mode=bh.BH_MODE_BF16_SPLIT, steps=30)
+    tids, pools = {}, {}
+    for N in boxes:
+        tpls = [synth.blob_template(synth.rng_for(40 + N, t), 60, 1.5 * N / 32, 0.75 * N / 2) for t in range(2)]
+        for t, tpl in enumerate(tpls):
+            tids[(N, t)] = srv.add_template(synth.render(N, tpl).astype(np.float32))
+        base = np.stack([synth.degrade(synth.render(N, tpls[j % 2], synth.uniform_quaternions(synth.rng_for(60 + N, j), 1)[0]),
+                                       synth.rng_for(70 + N, j), 0.1, 60.0) for j in range(64)]).astype(np.float32)
+        pools[N] = np.ascontiguousarray(np.tile(base, (8, 1, 1, 1)))
+    for N in boxes:  # first use of every plan and kernel variant
+        srv.wait(srv.submit(tids[(N, 0)], pools[N][:4], 16, seed=1), timeout_ms=600000)
+    setup_s = time.perf_counter() - t_setup
+    subm = []
+    t0 = time.perf_counter()
+    nxt = t0
+    while nxt - t0 < seconds:
+        now = time.perf_counter()
+        if nxt > now:
+            time.sleep(nxt - now)
+        N = boxes[int(rng.integers(0, 4))]
+        B = int(min(512, max(1, round(math.exp(rng.uniform(0.0, math.log(512.0)))))))
+        off = int(rng.integers(0, 512 - B + 1))
+        ts = time.perf_counter()
+        tk = srv.submit(tids[(N, int(rng.integers(0, 2)))], pools[N][off:off + B], 16, seed=int(rng.integers(1 << 62)))
+        subm.append((tk, B, N, ts))
+        nxt += rng.exponential(1.0 / rate)
+    lat, done_t = [], []
+    for tk, B, N, ts in subm:
+        l_ms = srv.wait(tk, timeout_ms=600000)[2]
+        lat.append(l_ms)
+        done_t.append(ts + l_ms / 1e3)
+    total = sum(b for _, b, _, _ in subm)
+    span = max(done_t) - t0
+    st = srv.stats()
+    srv.destroy()
+    p50, p99 = (float(x) for x in np.percentile(lat, [50, 99]))
+    return {"requests": len(subm), "subtomograms": total, "offered_req_per_s": rate, "seconds": seconds,
+            "throughput": total / span, "unit": UNIT, "p50_ms": p50, "p99_ms": p99,
+            "mean_subtomograms_per_request": total / max(1, len(subm)), "batches": int(st["batches"]),
+            "setup_s": setup_s,
+            "mix": "boxes 24/32/48/64 (l<=N/2, bands N/8-N/4-N/2), 1-512 subtomograms log-uniform, 16 starts, "
+                   "8 resident templates, SNR 0.1, +-60 deg wedge, BF16-split expansion"}
+
+
 def angle_deg(q1, q2):
     import numpy as np
     d = np.abs(np.sum(q1 * q2, axis=1) / (np.linalg.norm(q1, axis=1) * np.linalg.norm(q2, axis=1)))
@@ -318,6 +375,7 @@ def main():
     ap.add_argument("--count", type=int, default=None, help="subtomograms per GPU (default: the workload's)")
     ap.add_argument("--form", choices=["both", "bf16split", "fp32"], default="both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,6 +460,8 @@ def main():
         line["accuracy"] = acc
         if base is not None:
             line["cpu_baseline"] = base
+        if world == 1 and args.serve_seconds > 0:
+            line["serving"] = serving_leg(args.serve_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -31,6 +31,7 @@
 //
 // Work split: one CTA per subtomogram; lane group of G threads per start; within a row m the 2m+1
 // orbits are dealt round-robin to the G lanes, which reduce their partial sums by xor-shuffles.
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -449,10 +450,22 @@ __global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, i
 
 size_t table_bytes(int Lb) { return (size_t)tab_base(Lb + 1, Lb) * sizeof(float4); }
 
+// Raise a kernel's dynamic shared-memory limit only when a larger size is requested, so that launches
+// recorded into a CUDA graph after a first (warm-up) call make no attribute calls.
+template <typename K>
+int ensure_smem(K kernel, std::atomic<int>& have, size_t smem) {
+  if ((int)smem <= have.load()) return BH_OK;
+  BH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  have.store((int)smem);
+  return BH_OK;
+}
+
 template <int G, int NT>
 int launch_align_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
-  BH_CUDA_TRY(cudaFuncSetAttribute(k_align<G, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BH_CUDA_TRY(cudaFuncSetAttribute(k_align<G, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  static std::atomic<int> have{0};
+  int st = ensure_smem(k_align<G, NT>, have, smem);
+  if (st != BH_OK) return st;
   k_align<G, NT><<<a.B, NT, smem, stream>>>(a);
   BH_CHECK_LAUNCH();
   return BH_OK;
@@ -465,8 +478,9 @@ int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stre
   const size_t smem = std::max(table_bytes(a.Lb), score_only ? (size_t)16 : sel);
   if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
   if (score_only) {
-    BH_CUDA_TRY(cudaFuncSetAttribute(k_score<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BH_CUDA_TRY(cudaFuncSetAttribute(k_score<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    static std::atomic<int> have{0};
+    int st = ensure_smem(k_score<G>, have, smem);
+    if (st != BH_OK) return st;
     k_score<G><<<a.B, threads, smem, stream>>>(a, L);
     BH_CHECK_LAUNCH();
     return BH_OK;
@@ -499,8 +513,9 @@ template <int G>
 int launch_refine_g(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
   const int threads = round_up(K * G, 32);
   const size_t smem = table_bytes(a.Lb);
-  BH_CUDA_TRY(cudaFuncSetAttribute(k_refine64<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BH_CUDA_TRY(cudaFuncSetAttribute(k_refine64<G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  static std::atomic<int> have{0};
+  int st = ensure_smem(k_refine64<G>, have, smem);
+  if (st != BH_OK) return st;
   k_refine64<G><<<a.B, threads, smem, stream>>>(a, L, K, p->d_coef64, p->d_lbin64);
   BH_CHECK_LAUNCH();
   return BH_OK;
@@ -518,10 +533,13 @@ int launch_refine(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream
   }
 }
 
-// Default lanes per start (before autotuning): aim at 64 threads per CTA.
-int default_group(int S) {
+// Default lanes per start (before autotuning): about 512 resident threads per SM, given how many orbit
+// tables of band Lb fit in an SM's 227 KB of shared memory (at most 8 CTAs).
+int default_group(int S, int Lb) {
+  const int ctas = std::max(1, std::min(8, (int)(232448 / std::max<size_t>(1, table_bytes(Lb)))));
+  const int want = std::max(32, 512 / ctas);
   int G = 1;
-  while (G < 16 && S * G < 64 && S * G * 2 <= kMaxThreads) G *= 2;
+  while (G < 16 && S * G < want && round_up(S * G * 2, 32) <= kMaxThreads) G *= 2;
   return G;
 }
 
@@ -582,7 +600,7 @@ extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* s
   a.lbin = p->d_lbin;
   a.score_out = score;
   a.grad_out = grad;
-  int G = default_group(S);
+  int G = default_group(S, L);
   return launch_align(a, G, true, L, static_cast<cudaStream_t>(stream));
 }
 
@@ -633,7 +651,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   }
   if (G == 0) {
     auto it = p->align_group.find({a.Lb, S});
-    G = (it != p->align_group.end()) ? it->second : default_group(S);
+    G = (it != p->align_group.end()) ? it->second : default_group(S, a.Lb);
   }
   if (round_up(S * G, 32) > kMaxThreads) return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
   st = launch_align(a, G, false, 0, static_cast<cudaStream_t>(stream));

@@ -173,3 +173,79 @@ def make_workload(name: str, count: int | None = None, first: int = 0, master: i
         starts[j] = uniform_quaternions(rng_for(3, p, master), S).astype(np.float32)
     return Workload(name, N, Lmax, math.pi * N / 2, list(stages), steps, S, template, vols, q_true, starts,
                     {"blobs": nb, "sigma": sigma, "snr": snr, "wedge_deg": wedge, "first": first})
+
+
+# ---------------------------------------------------------------------------------- mixed batch
+@dataclass
+class ClassWorkload:
+    """One box class of a mixed batch: its templates and particles (sorted by start count)."""
+
+    N: int
+    Lmax: int
+    lam_max: float
+    stages: list
+    steps: int
+    templates: np.ndarray  # (n_templates, N, N, N) float32
+    vols: np.ndarray  # (B, N, N, N) float32
+    tmpl_index: np.ndarray  # (B,) int32
+    q_true: np.ndarray  # (B, 4)
+    S: np.ndarray  # (B,) starts per particle, ascending
+    starts: np.ndarray  # (B, max S, 4) float32 (rows beyond S[b] unused)
+
+    @property
+    def B(self) -> int:
+        return self.vols.shape[0]
+
+    def groups(self):
+        """Contiguous (first, count, S) runs of equal start count."""
+        out, b = [], 0
+        while b < self.B:
+            e = b
+            while e < self.B and self.S[e] == self.S[b]:
+                e += 1
+            out.append((b, e - b, int(self.S[b])))
+            b = e
+        return out
+
+
+# mixed batch: (box edge, count) per class; bands Lmax/4 -> Lmax/2 -> Lmax with Lmax = N/2
+MIXED_CLASSES = [(24, 3000), (40, 2000), (64, 1000)]
+MIXED_BLOBS = [40, 93, 146, 200]
+
+
+def make_mixed(scale: float = 1.0, distinct: int | None = None, master: int = MASTER_SEED) -> list:
+    """Batched uneven workload: classes of 24^3 (l <= 12), 40^3 (l <= 20) and 64^3 (l <= 32) subtomograms,
+    4 blob templates per class (40-200 blobs), SNR ~ U[0.03, 0.2], wedge half-angle ~ U[50, 70] deg,
+    starts per particle ~ uniform on {8, 16, 32}, 30 steps per band.  `scale` multiplies the class
+    counts; with `distinct`, only that many particles per class are generated and the rest repeat them."""
+    out = []
+    for ci, (N, count) in enumerate(MIXED_CLASSES):
+        count = max(1, int(round(count * scale)))
+        L = N // 2
+        sigma = 1.2 + 0.8 * (N - 16) / 48
+        tpls = [blob_template(rng_for(10 + ci, t, master), nb, sigma, 0.75 * N / 2) for t, nb in enumerate(MIXED_BLOBS)]
+        templates = np.stack([render(N, t) for t in tpls]).astype(np.float32)
+        n_gen = count if distinct is None else min(count, distinct)
+        vols = np.empty((n_gen, N, N, N), dtype=np.float32)
+        tidx = np.empty(n_gen, dtype=np.int32)
+        q_true = np.empty((n_gen, 4))
+        S = np.empty(n_gen, dtype=np.int32)
+        starts = np.zeros((n_gen, 32, 4), dtype=np.float32)
+        for j in range(n_gen):
+            rng = rng_for(20 + ci, j, master)
+            tidx[j] = rng.integers(0, len(tpls))
+            q = uniform_quaternions(rng, 1)[0]
+            q_true[j] = q
+            snr = rng.uniform(0.03, 0.2)
+            wedge = rng.uniform(50.0, 70.0)
+            vols[j] = degrade(render(N, tpls[tidx[j]], q), rng, snr, wedge).astype(np.float32)
+            S[j] = (8, 16, 32)[rng.integers(0, 3)]
+            starts[j, :S[j]] = uniform_quaternions(rng_for(30 + ci, j, master), S[j]).astype(np.float32)
+        if n_gen < count:
+            rep = np.arange(count) % n_gen
+            vols, tidx, q_true, S, starts = vols[rep], tidx[rep], q_true[rep], S[rep], starts[rep]
+        order = np.argsort(S, kind="stable")
+        stages = [s for s in (L // 4, L // 2, L) if s >= 1]
+        out.append(ClassWorkload(N, L, math.pi * N / 2, stages, 30, templates, vols[order], tidx[order],
+                                 q_true[order], S[order], starts[order]))
+    return out
