@@ -224,7 +224,13 @@ def run_ours(args, rank, world, device):
 
     from paper_2509_01180_gb300 import replicas
     count = args.count or synth.CONFIGS[args.workload][-1]
-    w = synth.make_workload(args.workload, count=count, first=replicas.shard_first(rank, count))
+    first = replicas.shard_first(rank, count)
+    if args.distinct and args.distinct < count:
+        w = synth.make_workload(args.workload, count=args.distinct, first=first)
+        rep = np.arange(count) % args.distinct
+        w.vols, w.q_true, w.starts = np.ascontiguousarray(w.vols[rep]), w.q_true[rep], np.ascontiguousarray(w.starts[rep])
+    else:
+        w = synth.make_workload(args.workload, count=count, first=first)
     B = w.B
     forms = {"bf16split": bh.BH_MODE_BF16_SPLIT, "fp32": bh.BH_MODE_FP32}
     order = [args.form] if args.form != "both" else ["bf16split", "fp32"]
@@ -245,10 +251,26 @@ def run_ours(args, rank, world, device):
         quat = torch.empty((B, 4), dtype=torch.float32, device=device)
         score = torch.empty((B,), dtype=torch.float32, device=device)
 
+        sq = torch.empty((B, w.S, 4), dtype=torch.float32, device=device) if args.refine else None
+        ss = torch.empty((B, w.S), dtype=torch.float32, device=device) if args.refine else None
+
+        def align_call():
+            if args.refine:
+                bh.lib().bh_align_batch  # noqa: B018
+                o = bh.AlignOpts()
+                o.refine_fp64 = args.refine
+                o.start_quat_out, o.start_score_out = sq.data_ptr(), ss.data_ptr()
+                st = (bh.ctypes.c_int * len(w.stages))(*w.stages)
+                bh._check(bh.lib().bh_align_batch(plan.handle, tmpl.data_ptr(), coeffs.data_ptr(), B, starts.data_ptr(),
+                                                  w.S, st, len(w.stages), w.steps, quat.data_ptr(), score.data_ptr(),
+                                                  bh.ctypes.byref(o), stream.cuda_stream), "bh_align_batch")
+            else:
+                bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
+                                  stream=stream)
+
         def step():
             bh.bh_expand(plan, vols, coeffs, stream=stream)
-            bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
-                              stream=stream)
+            align_call()
 
         for _ in range(args.warmup):
             step()
@@ -261,8 +283,7 @@ def run_ours(args, rank, world, device):
                 ev[k][0].record(stream)
                 bh.bh_expand(plan, vols, coeffs, stream=stream)
                 ev[k][1].record(stream)
-                bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
-                                  stream=stream)
+                align_call()
                 ev[k][2].record(stream)
                 flush.zero_()  # evict L2 between timed steps (not timed)
             torch.cuda.synchronize(device)
@@ -284,8 +305,7 @@ def run_ours(args, rank, world, device):
             e0.record(stream)
             dv.copy_(hv, non_blocking=True)
             bh.bh_expand(plan, dv, coeffs, stream=stream)
-            bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
-                              stream=stream)
+            align_call()
             hq.copy_(quat, non_blocking=True)
             hs.copy_(score, non_blocking=True)
             e1.record(stream)
@@ -359,6 +379,47 @@ def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
                    "8 resident templates, SNR 0.1, +-60 deg wedge, BF16-split expansion"}
 
 
+def run_mixed(args, device) -> dict:
+    """Batched uneven form: the whole mixed batch (3 box classes, 4 templates each, 8/16/32 starts) is one
+    CUDA-graph launch per step; value = subtomograms of the batch / graph time."""
+    import numpy as np
+    import torch
+
+    from paper_2509_01180_gb300 import mixed, synth
+    classes = synth.make_mixed(scale=args.mixed_scale, distinct=args.distinct or None)
+    mb = mixed.MixedBatch(classes, device)
+    mb.capture()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(args.warmup):
+        mb.replay()
+    torch.cuda.synchronize(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(device.index or 0) as clk:
+        for e0, e1 in ev:
+            e0.record(stream)
+            mb.replay()
+            e1.record(stream)
+            flush.zero_()
+        torch.cuda.synchronize(device)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    res = mb.results()
+    acc = []
+    for cw, (q, _) in zip(classes, res):
+        acc.append(float(np.median(angle_deg(q.astype(np.float64), cw.q_true * np.array([1, -1, -1, -1])))))
+    total = mb.total
+    desc = "; ".join(f"{cw.B} x {cw.N}^3 l<={cw.Lmax} bands {'-'.join(map(str, cw.stages))} "
+                     f"S groups {[g[2] for g in cw.groups()]}" for cw in classes)
+    mb.destroy()
+    return {"metric": METRIC, "value": total / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16-split/fp32", "data": "synthetic", "gpu_launches": mb.launches_per_replay() * args.steps,
+            "config": {"workload": f"mixed batch ({desc}), 4 templates (40-200 blobs) per class, SNR U[0.03,0.2], "
+                                   f"wedge U[50,70] deg, 30 steps, one CUDA-graph launch per step",
+                       "l2": "flushed between timed steps"},
+            "accuracy": {"median_angle_vs_truth_deg_by_class": acc}, "clocks": clk.summary()}
+
+
 def angle_deg(q1, q2):
     import numpy as np
     d = np.abs(np.sum(q1 * q2, axis=1) / (np.linalg.norm(q1, axis=1) * np.linalg.norm(q2, axis=1)))
@@ -376,6 +437,9 @@ def main():
     ap.add_argument("--form", choices=["both", "bf16split", "fp32"], default="both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
+    ap.add_argument("--mixed-scale", type=float, default=1.0, help="class-count multiplier of the mixed workload")
+    ap.add_argument("--distinct", type=int, default=0, help="generate only this many distinct phantoms and tile them")
+    ap.add_argument("--refine", type=int, default=None, help="FP64 re-scoring of the K best starts (precision form)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -397,10 +461,17 @@ def main():
 
     # the oracle's process pool is spawned before the first GPU call
     base = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "batch32":
         from paper_2509_01180_gb300 import synth
         base = cpu_baseline(synth.make_workload(args.workload, count=8))
 
+    if args.refine is None:
+        args.refine = 4 if args.workload == "precision64" else 0
+    if args.workload == "mixed":
+        line = run_mixed(args, device)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     w, res = run_ours(args, rank, world, device)
     if rank == 0:
         main_form = "bf16split" if "bf16split" in res else next(iter(res))
@@ -432,11 +503,13 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["t_tot"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16-split/fp32" if main_form == "bf16split" else "fp32", "data": "synthetic",
+            "dtype": ("bf16-split/fp32" if main_form == "bf16split" else "fp32") + ("+fp64-rescore" if args.refine else ""),
+            "data": "synthetic" + (f" ({args.distinct} distinct phantoms tiled)" if args.distinct else ""),
             "config": {"workload": describe(w), "form": main_form,
                        "expansion": "tcgen05 BF16 hi/lo split, FP32 accumulate" if main_form == "bf16split"
                        else "FP32 FFMA", "ascent": "FP32", "l2": "flushed between timed steps (256 MB write)",
                        "template": "expanded once before timing (resident)",
+                       "fp64_rescore_top_k": args.refine,
                        "autotuned": {"align_lanes_per_start": r["tune"]["align_group"],
                                      "gemm_n_tile": r["tune"]["gemm_bn"]},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

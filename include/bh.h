@@ -164,6 +164,8 @@ typedef struct {
   int n_templates;        /* rows in `tmpl` when tmpl_index is given */
   float* start_quat_out;  /* device, B * S * 4 floats or NULL: final rotation of every start */
   float* start_score_out; /* device, B * S floats or NULL: final score of every start */
+  int starts_per_thread;  /* 0 = autotuned; 1, or 2 (S even: each thread advances two starts' recursions
+                             through every orbit, sharing the table loads and coefficients) */
   int refine_fp64;        /* K in 0..64: after the FP32 ascent, re-score the K best starts (by FP32
                              score) at the last band with the d-recursion, seeds, phases and sums in
                              FP64 and select among them on the FP64 score (score_out then holds it,
@@ -193,7 +195,9 @@ int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int
 
 /* ------------------------------------------------------------------ autotuning */
 typedef struct {
-  int align_group;  /* lanes per start chosen for (band stages[nstages-1], S) */
+  int align_group;  /* lanes per start (per pair of starts when align_starts_per_thread = 2) chosen for
+                       (band stages[nstages-1], S) */
+  int align_starts_per_thread;
   float align_ms;   /* its time for B subtomograms */
   int gemm_bn;      /* N tile of the tensor-core expansion GEMM (BF16 mode; 0 in FP32 mode) */
   float expand_ms;  /* bh_expand time for B volumes with that tile */

@@ -40,7 +40,7 @@ class PlanOpts(ctypes.Structure):
 class AlignOpts(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int), ("tmpl_index", ctypes.c_void_p), ("n_templates", ctypes.c_int),
                 ("start_quat_out", ctypes.c_void_p), ("start_score_out", ctypes.c_void_p),
-                ("refine_fp64", ctypes.c_int)]
+                ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int)]
 
 
 _lib = None
@@ -187,7 +187,7 @@ def bh_score_grad(plan: Plan, tmpl, sub, quats, L: int, with_grad: bool = True, 
 # ------------------------------------------------------------------ alignment
 def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
                    n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None,
-                   refine_fp64: int = 0):
+                   refine_fp64: int = 0, starts_per_thread: int = 0):
     """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
     import torch
     B, S = starts.shape[0], starts.shape[1]
@@ -200,6 +200,7 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
     o = AlignOpts()
     o.group = group
+    o.starts_per_thread = starts_per_thread
     o.refine_fp64 = refine_fp64
     sq = ss = None
     if per_start or refine_fp64:
@@ -226,8 +227,8 @@ def bh_random_starts(seed: int, B: int, S: int) -> np.ndarray:
 
 # ------------------------------------------------------------------ serving
 class TuneResult(ctypes.Structure):
-    _fields_ = [("align_group", ctypes.c_int), ("align_ms", ctypes.c_float), ("gemm_bn", ctypes.c_int),
-                ("expand_ms", ctypes.c_float)]
+    _fields_ = [("align_group", ctypes.c_int), ("align_starts_per_thread", ctypes.c_int), ("align_ms", ctypes.c_float),
+                ("gemm_bn", ctypes.c_int), ("expand_ms", ctypes.c_float)]
 
 
 def bh_autotune(plan: Plan, B: int, S: int, stages, steps: int) -> dict:

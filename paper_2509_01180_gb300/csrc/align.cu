@@ -337,6 +337,196 @@ __global__ void __launch_bounds__(512, 1) k_score(const AlignArgs a, int L) {
   }
 }
 
+// ---------------------------------------------------------------------------- C starts per thread
+// The same evaluation for C rotations at once (C starts of one subtomogram): each orbit-step loads the
+// table entry, the per-band constants and the rational coefficient g once and advances C independent
+// recursions, so the shared part of the step is paid once per C starts and every thread carries C
+// independent FMA chains.
+template <int G, int C>
+__device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
+                               const float* __restrict__ lbin, Eval (&out)[C]) {
+  float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
+  float2 es[C], ed[C], EsG[C], edG[C], Ed2[C], Uq[C], Wrow[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
+    const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+    es[j] = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+    ed[j] = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+    xb[j] = (cb - sb) * (cb + sb);
+    sinb[j] = 2.f * cb * sb;
+    const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
+    lcc[j] = log2f(cbc);
+    lss[j] = log2f(sbc);
+    rcs[j] = cbc / sbc;
+    rsc[j] = sbc / cbc;
+    const float2 Es = cconj(es[j]);
+    EsG[j] = cpow(Es, G);
+    edG[j] = cpow(ed[j], G);
+    const float2 Ed = cconj(ed[j]);
+    Ed2[j] = cmul(Ed, Ed);
+    Uq[j] = cpow(Es, qg);
+    Wrow[j] = cpow(ed[j], qg);
+  }
+  float S[C], Sa[C], Sb[C], Sg[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
+  for (int m = 0; m <= L; ++m) {
+    const int w = 2 * m + 1;
+    const float4* rowp = tab + tab_base(m, Lb);
+    const float fm2 = (float)(m * m);
+    float2 U[C], W[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      U[j] = Uq[j];
+      W[j] = Wrow[j];
+    }
+    for (int n = qg - m; n <= m; n += G) {
+      const float lb = __ldg(lbin + m * kBinStride + m + n);
+      const float fa = (float)(m + n), fd = (float)(m - n);
+      const bool odd = (m - n) & 1;
+      float e1[C], e2[C], p1[C], p2[C];
+      float a1r[C], a1i[C], a2r[C], a2i[C], b1r[C], b1i[C], b2r[C], b2i[C];
+      const float4* ep = rowp + (n + m);
+      float4 xv = *ep;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        float d = exp2f(lb + fa * lcc[j] + fd * lss[j]);
+        d = odd ? -d : d;
+        const float dp = 0.5f * d * (fd * rcs[j] - fa * rsc[j]);
+        a1r[j] = d * xv.x; a1i[j] = d * xv.y; a2r[j] = d * xv.z; a2i[j] = d * xv.w;
+        b1r[j] = dp * xv.x; b1i[j] = dp * xv.y; b2r[j] = dp * xv.z; b2i[j] = dp * xv.w;
+        e1[j] = d; e2[j] = 0.f; p1[j] = dp; p2[j] = 0.f;
+      }
+      const float mn = (float)(m * n), fn2 = (float)(n * n);
+      for (int l = m + 1; l <= L; ++l) {
+        ep += w;
+        const float4 k = c_ecoef[l];
+        xv = *ep;
+        const float g = (k.z - fm2) * (k.z - fn2) * k.y;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const float t = fmaf(-mn, k.x, xb[j]);
+          const float en = fmaf(t, e1[j], -g * e2[j]);
+          const float pn = fmaf(t, p1[j], -fmaf(sinb[j], e1[j], g * p2[j]));
+          e2[j] = e1[j]; e1[j] = en; p2[j] = p1[j]; p1[j] = pn;
+          a1r[j] = fmaf(en, xv.x, a1r[j]); a1i[j] = fmaf(en, xv.y, a1i[j]);
+          a2r[j] = fmaf(en, xv.z, a2r[j]); a2i[j] = fmaf(en, xv.w, a2i[j]);
+          b1r[j] = fmaf(pn, xv.x, b1r[j]); b1i[j] = fmaf(pn, xv.y, b1i[j]);
+          b2r[j] = fmaf(pn, xv.z, b2r[j]); b2i[j] = fmaf(pn, xv.w, b2i[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float2 P1 = cmul(U[j], W[j]), P2 = cmul(U[j], cconj(W[j]));
+        const float2 z1 = cmul(P1, make_float2(a1r[j], a1i[j])), z2 = cmul(P2, make_float2(a2r[j], a2i[j]));
+        S[j] += z1.x + z2.x;
+        Sa[j] += (float)m * z1.y + (float)n * z2.y;
+        Sg[j] += (float)n * z1.y + (float)m * z2.y;
+        Sb[j] += (P1.x * b1r[j] - P1.y * b1i[j]) + (P2.x * b2r[j] - P2.y * b2i[j]);
+        U[j] = cmul(U[j], EsG[j]);
+        W[j] = cmul(W[j], edG[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) Wrow[j] = cmul(Wrow[j], Ed2[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      S[j] += __shfl_xor_sync(0xffffffffu, S[j], o);
+      Sa[j] += __shfl_xor_sync(0xffffffffu, Sa[j], o);
+      Sb[j] += __shfl_xor_sync(0xffffffffu, Sb[j], o);
+      Sg[j] += __shfl_xor_sync(0xffffffffu, Sg[j], o);
+    }
+    const float2 eg = cmul(es[j], cconj(ed[j]));
+    const float Q = (sinb[j] > 1e-30f) ? (xb[j] * Sg[j] - Sa[j]) / sinb[j] : 0.f;
+    out[j].S = S[j];
+    out[j].gx = Sb[j] * eg.y + Q * eg.x;
+    out[j].gy = Sb[j] * eg.x - Q * eg.y;
+    out[j].gz = Sg[j];
+  }
+}
+
+// Marching ascent with C starts per thread: CTA of NT = roundup(S/C * G, 32) threads per subtomogram.
+template <int G, int C, int NT>
+__global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs a) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  const int chunk = threadIdx.x / G, qg = threadIdx.x % G;
+  const int nchunks = a.S / C;
+  const bool active = chunk < nchunks;
+  const int ce = active ? chunk : chunk % nchunks;
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
+  __syncthreads();
+  float4 q[C];
+  Eval cur[C];
+  float h[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    q[j] = qnormalize(a.starts[(size_t)p * a.S + ce * C + j]);
+    cur[j].S = cur[j].gx = cur[j].gy = cur[j].gz = 0.f;
+  }
+  for (int st = 0; st < a.nstages; ++st) {
+    const int L = a.stages[st];
+    const float hmax = 3.14159265358979f / (float)L;
+#pragma unroll
+    for (int j = 0; j < C; ++j) h[j] = 0.5f * hmax;
+    eval_rotations<G, C>(smem_tab, a.Lb, L, q, qg, a.lbin, cur);
+    for (int t = 0; t < a.steps; ++t) {
+      float4 qt[C];
+      bool stop[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float gn = sqrtf(cur[j].gx * cur[j].gx + cur[j].gy * cur[j].gy + cur[j].gz * cur[j].gz);
+        stop[j] = !(gn > 1e-12f * fabsf(cur[j].S));
+        const float inv = stop[j] ? 0.f : 1.f / gn;
+        float sh, ch;
+        sincosf(stop[j] ? 0.f : 0.5f * h[j], &sh, &ch);
+        const float4 dq = make_float4(ch, sh * cur[j].gx * inv, sh * cur[j].gy * inv, sh * cur[j].gz * inv);
+        qt[j] = qnormalize(qmul(q[j], dq));
+      }
+      Eval tr[C];
+      eval_rotations<G, C>(smem_tab, a.Lb, L, qt, qg, a.lbin, tr);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        if (!stop[j]) {
+          if (tr[j].S > cur[j].S) {
+            q[j] = qt[j];
+            cur[j] = tr[j];
+            h[j] = fminf(1.5f * h[j], hmax);
+          } else {
+            h[j] *= 0.5f;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float* sS = reinterpret_cast<float*>(smem_tab);
+  float4* sQ = reinterpret_cast<float4*>(sS + ((a.S + 3) & ~3));
+  if (active && qg == 0) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int s = chunk * C + j;
+      sS[s] = cur[j].S;
+      sQ[s] = q[j];
+      if (a.start_quat_out) a.start_quat_out[(size_t)p * a.S + s] = q[j];
+      if (a.start_score_out) a.start_score_out[(size_t)p * a.S + s] = cur[j].S;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int j = 1; j < a.S; ++j)
+      if (sS[j] > sS[best]) best = j;
+    a.quat_out[p] = sQ[best];
+    a.score_out[p] = sS[best];
+  }
+}
+
 // ---------------------------------------------------------------------------- FP64 re-scoring
 // The same evaluation with the d-recursion, its coefficients, the seeds, the phases and every sum in
 // FP64 (the shared-memory table stays FP32: P_l xi^l rounded once per entry).  Used to re-score the
@@ -498,6 +688,47 @@ int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stre
   }
 }
 
+template <int G, int NT>
+int launch_align_c2_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
+  static std::atomic<int> have{0};
+  int st = ensure_smem(k_align_c<G, 2, NT>, have, smem);
+  if (st != BH_OK) return st;
+  k_align_c<G, 2, NT><<<a.B, NT, smem, stream>>>(a);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+template <int G>
+int launch_align_c2_g(const AlignArgs& a, cudaStream_t stream) {
+  const int threads = round_up((a.S / 2) * G, 32);
+  const size_t sel = (size_t)((a.S + 3) & ~3) * sizeof(float) + (size_t)a.S * sizeof(float4);
+  const size_t smem = std::max(table_bytes(a.Lb), sel);
+  if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
+  switch (threads) {
+    case 32: return launch_align_c2_nt<G, 32>(a, smem, stream);
+    case 64: return launch_align_c2_nt<G, 64>(a, smem, stream);
+    case 96:
+    case 128: return launch_align_c2_nt<G, 128>(a, smem, stream);
+    case 160:
+    case 192:
+    case 224:
+    case 256: return launch_align_c2_nt<G, 256>(a, smem, stream);
+    default: return launch_align_c2_nt<G, 512>(a, smem, stream);
+  }
+}
+
+// Two starts per thread (S even): G lanes per pair of starts.
+int launch_align_c2(const AlignArgs& a, int G, cudaStream_t stream) {
+  if (a.S % 2) return fail(BH_ERR_ARG, "two starts per thread need an even S (S=%d)", a.S);
+  switch (G) {
+    case 2: return launch_align_c2_g<2>(a, stream);
+    case 4: return launch_align_c2_g<4>(a, stream);
+    case 8: return launch_align_c2_g<8>(a, stream);
+    case 16: return launch_align_c2_g<16>(a, stream);
+    default: return fail(BH_ERR_ARG, "group %d not in {2,4,8,16} for two starts per thread", G);
+  }
+}
+
 int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t stream) {
   switch (G) {
     case 1: return launch_align_g<1>(a, score_only, L, stream);
@@ -634,7 +865,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   a.lbin = p->d_lbin;
   a.quat_out = reinterpret_cast<float4*>(quat_out);
   a.score_out = score_out;
-  int G = 0;
+  int G = 0, C = 0;
   if (opts) {
     if (opts->tmpl_index) {
       if (opts->n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d with tmpl_index", opts->n_templates);
@@ -644,6 +875,8 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     a.start_quat_out = reinterpret_cast<float4*>(opts->start_quat_out);
     a.start_score_out = opts->start_score_out;
     G = opts->group;
+    C = opts->starts_per_thread;
+    if (C < 0 || C > 2) return fail(BH_ERR_ARG, "starts_per_thread=%d not in {0,1,2}", C);
     if (opts->refine_fp64 < 0 || opts->refine_fp64 > kMaxRefine)
       return fail(BH_ERR_ARG, "refine_fp64=%d outside 0..%d", opts->refine_fp64, kMaxRefine);
     if (opts->refine_fp64 > 0 && (!opts->start_quat_out || !opts->start_score_out))
@@ -651,10 +884,23 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   }
   if (G == 0) {
     auto it = p->align_group.find({a.Lb, S});
-    G = (it != p->align_group.end()) ? it->second : default_group(S, a.Lb);
+    if (it != p->align_group.end()) {
+      G = it->second.first;
+      if (C == 0) C = it->second.second;
+    } else {
+      G = default_group(S, a.Lb);
+    }
   }
-  if (round_up(S * G, 32) > kMaxThreads) return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
-  st = launch_align(a, G, false, 0, static_cast<cudaStream_t>(stream));
+  if (C == 0) C = 1;
+  if (C == 2) {
+    if (round_up((S / 2) * G, 32) > kMaxThreads)
+      return fail(BH_ERR_ARG, "S/2*group = %d exceeds %d threads", (S / 2) * G, kMaxThreads);
+    st = launch_align_c2(a, G, static_cast<cudaStream_t>(stream));
+  } else {
+    if (round_up(S * G, 32) > kMaxThreads)
+      return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
+    st = launch_align(a, G, false, 0, static_cast<cudaStream_t>(stream));
+  }
   if (st != BH_OK || !opts || opts->refine_fp64 == 0) return st;
   return launch_refine(a, a.Lb, std::min(opts->refine_fp64, S), p, static_cast<cudaStream_t>(stream));
 }
@@ -697,12 +943,16 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
   AT_TRY(cudaMemsetAsync(coef, 0x3C, (size_t)B * p->Nb * 8, st));
   AT_TRY(cudaMemsetAsync(tmpl, 0x3C, (size_t)p->Nb * 8, st));
   AT_TRY(cudaMemsetAsync(starts, 0x3C, (size_t)B * S * 16, st));
-  int best_g = 0;
+  int best_g = 0, best_c = 1;
   float best_ms = 1e30f;
-  for (int G : {1, 2, 4, 8, 16}) {
-    if (round_up(S * G, 32) > kMaxThreads) continue;
+  const int cand[][2] = {{1, 1}, {2, 1}, {4, 1}, {8, 1}, {16, 1}, {2, 2}, {4, 2}, {8, 2}, {16, 2}};
+  for (const auto& gc : cand) {
+    const int G = gc[0], C = gc[1];
+    if (C == 2 && (S % 2)) continue;
+    if (round_up((S / C) * G, 32) > kMaxThreads) continue;
     bh_align_opts o{};
     o.group = G;
+    o.starts_per_thread = C;
     int rc = BH_OK;
     for (int it = 0; it < 2 && rc == BH_OK; ++it)
       rc = bh_align_batch(p, tmpl, coef, B, starts, S, stages, nstages, steps, quat, score, &o, st);
@@ -717,20 +967,21 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
     if (ms < best_ms) {
       best_ms = ms;
       best_g = G;
+      best_c = C;
     }
   }
   if (best_g == 0) {
     cleanup();
     return fail(BH_ERR_UNSUPPORTED, "no alignment variant runs for S=%d band %d", S, Lb);
   }
-  p->align_group[{Lb, S}] = best_g;
+  p->align_group[{Lb, S}] = {best_g, best_c};
   int best_bn = 0;
   float best_ems = 0.f;
   if (p->mode == BH_MODE_BF16_SPLIT) {
     AT_TRY(cudaMalloc(&vols, (size_t)B * N3 * 4));
     AT_TRY(cudaMemsetAsync(vols, 0x3C, (size_t)B * N3 * 4, st));
     best_ems = 1e30f;
-    for (int bn : {256, 128}) {
+    for (int bn : {128}) {
       int rc = set_gemm_bn(p, bn);
       for (int it = 0; it < 2 && rc == BH_OK; ++it) rc = bh_expand(p, vols, B, coef, st);
       if (rc != BH_OK) continue;
@@ -746,7 +997,7 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
         best_bn = bn;
       }
     }
-    int rc = set_gemm_bn(p, best_bn ? best_bn : 256);
+    int rc = set_gemm_bn(p, best_bn ? best_bn : 128);
     if (rc != BH_OK) {
       cleanup();
       return rc;
@@ -756,6 +1007,7 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
   cleanup();
   if (out) {
     out->align_group = best_g;
+    out->align_starts_per_thread = best_c;
     out->align_ms = best_ms;
     out->gemm_bn = best_bn;
     out->expand_ms = best_ems;

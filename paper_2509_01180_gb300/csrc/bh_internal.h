@@ -51,7 +51,7 @@ struct Layout {
 constexpr int kGemmBM = 128;
 constexpr int kGemmBK = 64;
 constexpr int kPadV = 64;    // V is padded to a multiple of the K block
-constexpr int kPadNb = 256;  // Nb is padded to a multiple of the widest N tile
+constexpr int kPadNb = 256;  // Nb is padded to a multiple of 256 (FP32 and tensor-core N tiles divide it)
 
 }  // namespace bh
 
@@ -72,16 +72,18 @@ struct bh_plan {
   float* d_X32 = nullptr;           // [M_cap][V_pad] gathered volumes (FP32 mode)
   __nv_bfloat16* d_Xhi = nullptr;   // [M_cap][V_pad] gathered volumes, hi part
   __nv_bfloat16* d_Xlo = nullptr;   // [M_cap][V_pad] lo part
-  float* d_C = nullptr;             // [M_cap][Nb_pad] real GEMM output
+  float* d_C = nullptr;             // [ksplit_max][M_cap][Nb_pad] real GEMM output (per K split)
   int* d_err = nullptr;             // device status word written by bounded waits
   float* d_P = nullptr;             // orbit-table scale P_l(m,n), layout [m][l][n] for l <= Lmax
   float2* d_coef = nullptr;         // (B_l, g_l) of the rescaled d recursion, same layout
   float* d_lbin = nullptr;          // 0.5 log2 C(2m, m+n) at [m][m+n], row stride 2 kMaxL + 1
   double2* d_coef64 = nullptr;      // FP64 copies of the two tables above (FP64 re-scoring)
   double* d_lbin64 = nullptr;
-  int gemm_bn = 256;                // N tile of the tensor-core GEMM
+  int gemm_bn = 128;                // N tile of the tensor-core GEMM
+  int num_sms = 152;                // SMs of the device (split-K sizing)
+  int ksplit_max = 1;               // K splits the GEMM-output scratch holds
   CUtensorMap tm_xhi, tm_xlo, tm_thi, tm_tlo;  // TMA descriptors (BF16 mode)
-  std::map<std::pair<int, int>, int> align_group;  // autotuned lanes-per-start by (top band, S)
+  std::map<std::pair<int, int>, std::pair<int, int>> align_group;  // autotuned (lanes, starts per thread) by (band, S)
 };
 
 namespace bh {

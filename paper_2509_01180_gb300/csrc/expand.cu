@@ -58,16 +58,20 @@ __global__ void k_gather(const float* __restrict__ vols, int B, long long N3, co
 
 // ---------------------------------------------------------------- real columns -> complex coefficients
 // slot[s] = (re source, im source), 1-based column index with sign, 0 = zero.
+// With split-K the GEMM leaves `splits` partial products `split_stride` floats apart; they are summed
+// here in split order (deterministic).
 __global__ void k_to_complex(const float* __restrict__ C, int ldc, int B, int Nb, const int2* __restrict__ slot,
-                             float2* __restrict__ out) {
+                             float2* __restrict__ out, int splits, size_t split_stride) {
   const int b = blockIdx.y;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || s >= Nb) return;
   const int2 src = slot[s];
-  const float* row = C + (size_t)b * ldc;
   float re = 0.f, im = 0.f;
-  if (src.x > 0) re = row[src.x - 1]; else if (src.x < 0) re = -row[-src.x - 1];
-  if (src.y > 0) im = row[src.y - 1]; else if (src.y < 0) im = -row[-src.y - 1];
+  for (int z = 0; z < splits; ++z) {
+    const float* row = C + (size_t)z * split_stride + (size_t)b * ldc;
+    if (src.x > 0) re += row[src.x - 1]; else if (src.x < 0) re -= row[-src.x - 1];
+    if (src.y > 0) im += row[src.y - 1]; else if (src.y < 0) im -= row[-src.y - 1];
+  }
   out[(size_t)b * Nb + s] = make_float2(re, im);
 }
 
@@ -76,16 +80,21 @@ __global__ void k_to_complex(const float* __restrict__ C, int ldc, int B, int Nb
 constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16, SG_PAD = 4;
 
 __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, const float* __restrict__ Bm,
-                                                  float* __restrict__ C, int M, int N, int K) {
+                                                  float* __restrict__ C, int M, int N, int K, int k_split,
+                                                  size_t split_stride) {
+  // split z of the grid covers K range [z k_split, min(K, (z+1) k_split)) and writes C + z split_stride
+  const int kbeg = blockIdx.z * k_split;
+  const int kend = min(K, kbeg + k_split);
+  C += (size_t)blockIdx.z * split_stride;
   __shared__ __align__(16) float As[SG_BK][SG_BM + SG_PAD];
   __shared__ __align__(16) float Bs[SG_BK][SG_BN + SG_PAD];
   const int tid = threadIdx.x;
   const int m0 = blockIdx.y * SG_BM, n0 = blockIdx.x * SG_BN;
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: rows lr and lr+64, k columns lk..lk+3
   const int tx = tid & 15, ty = tid >> 4;
-  const float* Ap0 = A + (size_t)(m0 + lr) * K + lk;
+  const float* Ap0 = A + (size_t)(m0 + lr) * K + kbeg + lk;
   const float* Ap1 = Ap0 + (size_t)64 * K;
-  const float* Bp0 = Bm + (size_t)(n0 + lr) * K + lk;
+  const float* Bp0 = Bm + (size_t)(n0 + lr) * K + kbeg + lk;
   const float* Bp1 = Bp0 + (size_t)64 * K;
   float acc[8][8];
 #pragma unroll
@@ -94,14 +103,15 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, c
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
   float4 a0 = __ldg(reinterpret_cast<const float4*>(Ap0)), a1 = __ldg(reinterpret_cast<const float4*>(Ap1));
   float4 b0 = __ldg(reinterpret_cast<const float4*>(Bp0)), b1 = __ldg(reinterpret_cast<const float4*>(Bp1));
-  for (int k0 = 0; k0 < K; k0 += SG_BK) {
+  const int klen = kend - kbeg;
+  for (int k0 = 0; k0 < klen; k0 += SG_BK) {
     __syncthreads();
     As[lk + 0][lr] = a0.x; As[lk + 1][lr] = a0.y; As[lk + 2][lr] = a0.z; As[lk + 3][lr] = a0.w;
     As[lk + 0][lr + 64] = a1.x; As[lk + 1][lr + 64] = a1.y; As[lk + 2][lr + 64] = a1.z; As[lk + 3][lr + 64] = a1.w;
     Bs[lk + 0][lr] = b0.x; Bs[lk + 1][lr] = b0.y; Bs[lk + 2][lr] = b0.z; Bs[lk + 3][lr] = b0.w;
     Bs[lk + 0][lr + 64] = b1.x; Bs[lk + 1][lr + 64] = b1.y; Bs[lk + 2][lr + 64] = b1.z; Bs[lk + 3][lr + 64] = b1.w;
     __syncthreads();
-    if (k0 + SG_BK < K) {  // prefetch the next K block into registers while computing this one
+    if (k0 + SG_BK < klen) {  // prefetch the next K block into registers while computing this one
       a0 = __ldg(reinterpret_cast<const float4*>(Ap0 + k0 + SG_BK));
       a1 = __ldg(reinterpret_cast<const float4*>(Ap1 + k0 + SG_BK));
       b0 = __ldg(reinterpret_cast<const float4*>(Bp0 + k0 + SG_BK));
@@ -244,116 +254,154 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-template <int BN>
-struct TcCfg {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Tensor-core GEMM with FP32 promotion of the accumulator.  Additions into the tcgen05 accumulator in
+// TMEM truncate, so their error grows with the number of accumulate steps (3 K/16 per output, ~2.6e4 at
+// a 64^3 box); here every KCHUNK K-blocks the MMA issuer switches to the other of two TMEM accumulators
+// (started afresh), and the four epilogue warps add each finished chunk into an FP32 running sum kept in
+// shared memory (one row per thread, rows padded by one float), then hand the TMEM buffer back.
+//   warp 4 lane 0: TMA producer (2-stage ring of A hi/lo and B hi/lo tiles, 128-byte swizzle)
+//   warp 5 lane 0: MMA issuer (three tcgen05.mma per 16-wide K step: hi*hi, hi*lo, lo*hi)
+//   warps 0-3:     epilogue (warp w owns TMEM lanes and tile rows 32w..32w+31)
+constexpr int PBN = 128, PST = 2, KCHUNK = 16;
+struct PCfg {
   static constexpr int BM = kGemmBM, BK = kGemmBK;
-  static constexpr int STAGES = (BN >= 256) ? 2 : 3;
-  static constexpr uint32_t A_BYTES = BM * BK * 2;
-  static constexpr uint32_t B_BYTES = BN * BK * 2;
+  static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = PBN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;  // + alignment slack
+  static constexpr int ROW = PBN + 1;  // padded running-sum row (floats)
+  static constexpr size_t SMEM = (size_t)PST * STAGE_BYTES + (size_t)BM * ROW * 4 + 1024;
 };
 
-// One 128 x BN output tile per CTA of 4 warps.  Warp 0 lane 0 issues TMA, warp 1 lane 0 issues MMAs,
-// all four warps read the accumulator (warp w owns TMEM lanes 32w..32w+31 = tile rows) and store it.
-template <int BN>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-              float* __restrict__ C, int ldc, int num_kb, int* __restrict__ err) {
-  using Cfg = TcCfg<BN>;
-  constexpr int ST = Cfg::STAGES;
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_tc_promoted(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                       const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                       float* __restrict__ C, int ldc, int num_kb_total, int kb_split, size_t split_stride,
+                       int* __restrict__ err) {
+  // split z of the grid covers K blocks [z kb_split, min(total, (z+1) kb_split)) and writes C + z split_stride
+  const int kb_first = blockIdx.z * kb_split;
+  const int num_kb = min(num_kb_total - kb_first, kb_split);
+  C += (size_t)blockIdx.z * split_stride;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST], done_bar;
+  float* acc = reinterpret_cast<float*>(smem + (size_t)PST * PCfg::STAGE_BYTES);
+  __shared__ __align__(8) uint64_t full_bar[PST], empty_bar[PST], accf_bar[2], acce_bar[2];
   __shared__ uint32_t tmem_base_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * Cfg::BM, n0 = blockIdx.x * BN;
-  auto sA_hi = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES; };
-  auto sA_lo = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES + Cfg::A_BYTES; };
-  auto sB_hi = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES; };
-  auto sB_lo = [&](int s) { return smem + (size_t)s * Cfg::STAGE_BYTES + 2 * Cfg::A_BYTES + Cfg::B_BYTES; };
+  const int m0 = blockIdx.y * PCfg::BM, n0 = blockIdx.x * PBN;
+  const int nchunks = (num_kb + KCHUNK - 1) / KCHUNK;
+  auto sA_hi = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES; };
+  auto sA_lo = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES + PCfg::A_BYTES; };
+  auto sB_hi = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES + 2 * PCfg::A_BYTES; };
+  auto sB_lo = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES + 2 * PCfg::A_BYTES + PCfg::B_BYTES; };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < ST; ++s) {
+    for (int s = 0; s < PST; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 128);
+    }
     mbar_fence_init();
   }
   if (warp == 0) {
-    tmem_alloc(&tmem_base_sh, BN);
+    tmem_alloc(&tmem_base_sh, 2 * PBN);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tacc = tmem_base_sh;
+  const uint32_t tbase = tmem_base_sh;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    int kb = 0;
-    for (; kb < num_kb; ++kb) {
-      const int s = kb % ST;
-      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
-      if (!mbar_wait(&empty_bar[s], ph ^ 1u, err, 101)) break;
-      mbar_arrive_expect_tx(&full_bar[s], Cfg::STAGE_BYTES);
-      const int kx = kb * Cfg::BK;
-      tma_load_2d(sA_hi(s), &tmAh, kx, m0, &full_bar[s]);
-      tma_load_2d(sA_lo(s), &tmAl, kx, m0, &full_bar[s]);
-      tma_load_2d(sB_hi(s), &tmBh, kx, n0, &full_bar[s]);
-      tma_load_2d(sB_lo(s), &tmBl, kx, n0, &full_bar[s]);
-    }
-    if (kb < num_kb) {
-      // gave up: let the copies already issued land before the CTA leaves (bounded again)
-      for (int j = (kb >= ST ? kb - ST : 0); j < kb; ++j) mbar_wait(&full_bar[j % ST], (uint32_t)(j / ST) & 1u, err, 102);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(Cfg::BM, BN);
-    for (int kb = 0; kb < num_kb; ++kb) {
-      const int s = kb % ST;
-      const uint32_t ph = (uint32_t)(kb / ST) & 1u;
-      if (!mbar_wait(&full_bar[s], ph, err, 103)) break;
-      tc_fence_after();
-      const uint64_t ah = sdesc_k_sw128(smem_u32(sA_hi(s))), al = sdesc_k_sw128(smem_u32(sA_lo(s)));
-      const uint64_t bh = sdesc_k_sw128(smem_u32(sB_hi(s))), bl = sdesc_k_sw128(smem_u32(sB_lo(s)));
-#pragma unroll
-      for (int k = 0; k < Cfg::BK / 16; ++k) {
-        const uint64_t adv = (uint64_t)(k * 32) >> 4;  // 16 BF16 = 32 bytes along K inside the swizzle atom
-        umma_bf16(tacc, ah + adv, bh + adv, idesc, (kb | k) != 0 ? 1u : 0u);
-        umma_bf16(tacc, ah + adv, bl + adv, idesc, 1u);
-        umma_bf16(tacc, al + adv, bh + adv, idesc, 1u);
+  if (warp == 4) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int kb = 0;
+      for (; kb < num_kb; ++kb) {
+        const int s = kb % PST;
+        const uint32_t ph = (uint32_t)(kb / PST) & 1u;
+        if (!mbar_wait(&empty_bar[s], ph ^ 1u, err, 111)) break;
+        mbar_arrive_expect_tx(&full_bar[s], PCfg::STAGE_BYTES);
+        const int kx = (kb_first + kb) * PCfg::BK;
+        tma_load_2d(sA_hi(s), &tmAh, kx, m0, &full_bar[s]);
+        tma_load_2d(sA_lo(s), &tmAl, kx, m0, &full_bar[s]);
+        tma_load_2d(sB_hi(s), &tmBh, kx, n0, &full_bar[s]);
+        tma_load_2d(sB_lo(s), &tmBl, kx, n0, &full_bar[s]);
       }
-      umma_commit(&empty_bar[s]);  // frees the stage once these MMAs have read it
+      if (kb < num_kb)  // gave up: let the copies already issued land before the CTA leaves (bounded)
+        for (int j = (kb >= PST ? kb - PST : 0); j < kb; ++j)
+          mbar_wait(&full_bar[j % PST], (uint32_t)(j / PST) & 1u, err, 112);
     }
-    umma_commit(&done_bar);  // accumulator complete (also on the error path: waits for issued MMAs)
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: TMEM -> registers -> global
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0, err, 104));  // warp-uniform before tcgen05.ld
-  tc_fence_after();
-  const int row = m0 + warp * 32 + lane;
-  float* crow = C + (size_t)row * ldc + n0;
-#pragma unroll 1
-  for (int c = 0; c < BN / 32; ++c) {
-    uint32_t r[32];
-    tmem_ld_32x32b_x32(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-    tmem_ld_wait();
-    if (ok) {
-      float4* dst = reinterpret_cast<float4*>(crow + c * 32);
+  } else if (warp == 5) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16_f32(PCfg::BM, PBN);
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1, use = c >> 1;
+        if (ok && !mbar_wait(&acce_bar[buf], (uint32_t)(use & 1) ^ 1u, err, 113)) ok = false;
+        tc_fence_after();
+        const uint32_t tacc = tbase + (uint32_t)(buf * PBN);
+        const int kb0 = c * KCHUNK, kb1 = min(num_kb, kb0 + KCHUNK);
+        for (int kb = kb0; ok && kb < kb1; ++kb) {
+          const int s = kb % PST;
+          const uint32_t ph = (uint32_t)(kb / PST) & 1u;
+          if (!mbar_wait(&full_bar[s], ph, err, 114)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ah = sdesc_k_sw128(smem_u32(sA_hi(s))), al = sdesc_k_sw128(smem_u32(sA_lo(s)));
+          const uint64_t bh = sdesc_k_sw128(smem_u32(sB_hi(s))), bl = sdesc_k_sw128(smem_u32(sB_lo(s)));
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        dst[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]), __uint_as_float(r[4 * i + 2]),
-                             __uint_as_float(r[4 * i + 3]));
+          for (int k = 0; k < PCfg::BK / 16; ++k) {
+            const uint64_t adv = (uint64_t)(k * 32) >> 4;
+            umma_bf16(tacc, ah + adv, bh + adv, idesc, (kb != kb0 || k != 0) ? 1u : 0u);
+            umma_bf16(tacc, ah + adv, bl + adv, idesc, 1u);
+            umma_bf16(tacc, al + adv, bh + adv, idesc, 1u);
+          }
+          umma_commit(&empty_bar[s]);
+        }
+        umma_commit(&accf_bar[buf]);  // chunk finished (or abandoned): the epilogue may read the buffer
+      }
+    }
+  } else {
+    // ---------------- epilogue warps 0-3: promote every chunk into the FP32 running sum
+    const int row = warp * 32 + lane;
+    float* arow = acc + (size_t)row * PCfg::ROW;
+    for (int j = 0; j < PBN; ++j) arow[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int buf = c & 1, use = c >> 1;
+      if (ok) ok = mbar_wait(&accf_bar[buf], (uint32_t)(use & 1), err, 115);
+      ok = __all_sync(0xffffffffu, ok);
+      tc_fence_after();
+#pragma unroll 1
+      for (int cc = 0; cc < PBN / 32; ++cc) {
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * PBN + cc * 32), r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) arow[cc * 32 + i] += __uint_as_float(r[i]);
+      }
+      tc_fence_before();
+      mbar_arrive(&acce_bar[buf]);
+    }
+    if (ok) {
+      float* crow = C + (size_t)(m0 + row) * ldc + n0;
+#pragma unroll 4
+      for (int j = 0; j < PBN; j += 4)
+        *reinterpret_cast<float4*>(crow + j) = make_float4(arow[j], arow[j + 1], arow[j + 2], arow[j + 3]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tacc, BN);
+  if (warp == 0) tmem_dealloc(tbase, 2 * PBN);
 }
 
 }  // namespace
@@ -438,7 +486,7 @@ int make_tensor_maps(bh_plan* p) {
 }
 
 int set_gemm_bn(bh_plan* p, int bn) {
-  if (bn != 128 && bn != 256) return fail(BH_ERR_ARG, "GEMM N tile %d not in {128, 256}", bn);
+  if (bn != 128) return fail(BH_ERR_ARG, "GEMM N tile %d: the promoted tensor-core GEMM uses 128", bn);
   if (p->mode != BH_MODE_BF16_SPLIT || p->gemm_bn == bn) {
     p->gemm_bn = bn;
     return BH_OK;
@@ -447,35 +495,37 @@ int set_gemm_bn(bh_plan* p, int bn) {
   return make_tensor_maps(p);
 }
 
-static int launch_gemm(bh_plan* p, int Mp, cudaStream_t stream) {
+// K splits for a pass of Mp rows: enough CTAs for about two waves over the SMs when the output tiles
+// alone are few, each split keeping at least 32 K-blocks (two promotion chunks), at most the plan's
+// scratch allows.
+static int choose_splits(const bh_plan* p, int Mp) {
+  const int tiles = (Mp / kGemmBM) * (p->Nb_pad / 128);
+  const int num_kb = p->V_pad / kGemmBK;
+  int s = (2 * p->num_sms + tiles - 1) / tiles;
+  s = std::min(s, std::max(1, num_kb / 32));
+  return std::max(1, std::min(s, p->ksplit_max));
+}
+
+static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
+  const size_t stride = (size_t)p->M_cap * p->Nb_pad;
   if (p->mode == BH_MODE_FP32) {
-    dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM);
-    k_sgemm_nt<<<grid, 256, 0, stream>>>(p->d_X32, p->d_T32, p->d_C, Mp, p->Nb_pad, p->V_pad);
+    const int k_split = round_up((p->V_pad + splits - 1) / splits, SG_BK);
+    dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM, (p->V_pad + k_split - 1) / k_split);  // every split has K work
+    k_sgemm_nt<<<grid, 256, 0, stream>>>(p->d_X32, p->d_T32, p->d_C, Mp, p->Nb_pad, p->V_pad, k_split, stride);
     BH_CHECK_LAUNCH();
     return BH_OK;
   }
   const int num_kb = p->V_pad / kGemmBK;
-  if (p->gemm_bn == 256) {
-    static bool attr = false;
-    if (!attr) {
-      BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)TcCfg<256>::SMEM));
-      attr = true;
-    }
-    dim3 grid(p->Nb_pad / 256, Mp / kGemmBM);
-    k_gemm_tc<256><<<grid, 128, TcCfg<256>::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
-                                                            p->Nb_pad, num_kb, p->d_err);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)TcCfg<128>::SMEM));
-      attr = true;
-    }
-    dim3 grid(p->Nb_pad / 128, Mp / kGemmBM);
-    k_gemm_tc<128><<<grid, 128, TcCfg<128>::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
-                                                            p->Nb_pad, num_kb, p->d_err);
+  const int kb_split = round_up((num_kb + splits - 1) / splits, KCHUNK);
+  static bool attr = false;
+  if (!attr) {
+    BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_promoted, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)PCfg::SMEM));
+    attr = true;
   }
+  dim3 grid(p->Nb_pad / PBN, Mp / kGemmBM, (num_kb + kb_split - 1) / kb_split);
+  k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
+                                                      p->Nb_pad, num_kb, kb_split, stride, p->d_err);
   BH_CHECK_LAUNCH();
   return BH_OK;
 }
@@ -507,27 +557,19 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
     BH_CHECK_LAUNCH();
     if (p->mode == BH_MODE_FP32) {
       dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM);
-      k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, scratch_c, Mp, p->Nb_pad, p->V_pad);
+      k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, scratch_c, Mp, p->Nb_pad, p->V_pad, p->V_pad, 0);
     } else {
       const int num_kb = p->V_pad / kGemmBK;
-      if (p->gemm_bn == 256) {
-        BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TcCfg<256>::SMEM));
-        dim3 grid(p->Nb_pad / 256, Mp / kGemmBM);
-        k_gemm_tc<256><<<grid, 128, TcCfg<256>::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c,
-                                                                p->Nb_pad, num_kb, p->d_err);
-      } else {
-        BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TcCfg<128>::SMEM));
-        dim3 grid(p->Nb_pad / 128, Mp / kGemmBM);
-        k_gemm_tc<128><<<grid, 128, TcCfg<128>::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c,
-                                                                p->Nb_pad, num_kb, p->d_err);
-      }
+      BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_promoted, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PCfg::SMEM));
+      dim3 grid(p->Nb_pad / PBN, Mp / kGemmBM);
+      k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c, p->Nb_pad,
+                                                          num_kb, num_kb, 0, p->d_err);
     }
     BH_CHECK_LAUNCH();
     dim3 g2((p->Nb + 255) / 256, Bc);
     k_to_complex<<<g2, 256, 0, stream>>>(scratch_c, p->Nb_pad, Bc, p->Nb, p->d_slot,
-                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb);
+                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb, 1, 0);
     BH_CHECK_LAUNCH();
   }
   return BH_OK;
@@ -552,11 +594,19 @@ extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, vo
     k_gather<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, p->d_X32, p->d_Xhi,
                                      p->d_Xlo);
     BH_CHECK_LAUNCH();
-    int st = launch_gemm(p, Mp, stream);
+    const int splits = choose_splits(p, Mp);
+    int st = launch_gemm(p, Mp, splits, stream);
     if (st != BH_OK) return st;
+    const int nkb = p->V_pad / kGemmBK;
+    const int used = (p->mode == BH_MODE_FP32)
+                         ? (p->V_pad + round_up((p->V_pad + splits - 1) / splits, SG_BK) - 1) /
+                               round_up((p->V_pad + splits - 1) / splits, SG_BK)
+                         : (nkb + round_up((nkb + splits - 1) / splits, KCHUNK) - 1) /
+                               round_up((nkb + splits - 1) / splits, KCHUNK);
     dim3 g2((p->Nb + 255) / 256, Bc);
     k_to_complex<<<g2, 256, 0, stream>>>(p->d_C, p->Nb_pad, Bc, p->Nb, p->d_slot,
-                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb);
+                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb, used,
+                                         (size_t)p->M_cap * p->Nb_pad);
     BH_CHECK_LAUNCH();
   }
   return BH_OK;

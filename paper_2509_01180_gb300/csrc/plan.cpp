@@ -396,7 +396,13 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_Xhi, sizeof(__nv_bfloat16) * x_elems), "cudaMalloc X hi"));
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_Xlo, sizeof(__nv_bfloat16) * x_elems), "cudaMalloc X lo"));
   }
-  PLAN_TRY(cuda_ok(cudaMalloc(&p->d_C, sizeof(float) * (size_t)p->M_cap * p->Nb_pad), "cudaMalloc C"));
+  // split-K capacity: about two waves over the SMs for a single 128-row pass, at most 8 splits
+  p->num_sms = prop.multiProcessorCount;
+  {
+    const int tiles = p->Nb_pad / 128;
+    p->ksplit_max = std::max(1, std::min(8, (2 * p->num_sms + tiles - 1) / tiles));
+  }
+  PLAN_TRY(cuda_ok(cudaMalloc(&p->d_C, sizeof(float) * (size_t)p->ksplit_max * p->M_cap * p->Nb_pad), "cudaMalloc C"));
   // ---- scale of the rescaled Wigner-d recursion: P_l(m,n) = prod_{j=m+1..l} j(2j-1)/sqrt((j^2-m^2)(j^2-n^2)),
   //      rows m = 0..Lmax, each [l = m..Lmax][n = -m..m]
   {

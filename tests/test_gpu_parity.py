@@ -311,3 +311,18 @@ def test_expand_gemm_tiles(dev, bn):
         assert rel_l2(got[b], ref[b]) < 1e-4
     p.destroy()
     del ctypes
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [bh.BH_MODE_FP32, bh.BH_MODE_BF16_SPLIT])
+def test_expand_64_box_matches_oracle(dev, mode):
+    """64^3 box, l <= 32 (K = 137 059 voxels per coefficient): the tensor-core path promotes its TMEM
+    accumulator to FP32 every 16 K-blocks, so its error stays at the split's ~1e-5 instead of growing
+    with the number of accumulate steps."""
+    rng = np.random.default_rng(640)
+    vols = rng.normal(size=(2, 64, 64, 64)).astype(np.float32)
+    p = plan_for(64, 32, mode)
+    got = to_c(bh.bh_expand(p, torch.from_numpy(vols).to(dev)))
+    ref = ball.expand(basis_for(64, 32), vols.astype(np.float64))
+    for b in range(2):
+        assert rel_l2(got[b], ref[b]) < 3e-5, (b, rel_l2(got[b], ref[b]))
