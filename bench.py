@@ -245,7 +245,10 @@ def run_ours(args, rank, world, device):
         t0 = time.perf_counter()
         plan = bh.bh_plan_create(w.N, w.Lmax, w.lam_max, forms[name], max_batch=min(B, 4096))
         plan_s = time.perf_counter() - t0
-        tune = bh.bh_autotune(plan, B, w.S, w.stages, w.steps)  # picks kernel variants (untimed setup)
+        if args.no_autotune:
+            tune = {"align_group": args.group, "align_starts_per_thread": args.starts_per_thread, "gemm_bn": 128}
+        else:
+            tune = bh.bh_autotune(plan, B, w.S, w.stages, w.steps)  # picks kernel variants (untimed setup)
         tmpl = bh.bh_expand(plan, tvol)[0].contiguous()
         coeffs = torch.empty((B, plan.Nb, 2), dtype=torch.float32, device=device)
         quat = torch.empty((B, 4), dtype=torch.float32, device=device)
@@ -266,7 +269,8 @@ def run_ours(args, rank, world, device):
                                                   bh.ctypes.byref(o), stream.cuda_stream), "bh_align_batch")
             else:
                 bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
-                                  stream=stream)
+                                  stream=stream, group=args.group if args.no_autotune else 0,
+                                  starts_per_thread=args.starts_per_thread if args.no_autotune else 0)
 
         def step():
             bh.bh_expand(plan, vols, coeffs, stream=stream)
@@ -438,6 +442,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
     ap.add_argument("--mixed-scale", type=float, default=1.0, help="class-count multiplier of the mixed workload")
+    ap.add_argument("--no-autotune", action="store_true", help="use --group/--starts-per-thread instead of tuning")
+    ap.add_argument("--group", type=int, default=4, help="lanes per start (group) with --no-autotune")
+    ap.add_argument("--starts-per-thread", type=int, default=2, help="starts per thread with --no-autotune")
     ap.add_argument("--distinct", type=int, default=0, help="generate only this many distinct phantoms and tile them")
     ap.add_argument("--refine", type=int, default=None, help="FP64 re-scoring of the K best starts (precision form)")
     args = ap.parse_args()
@@ -510,7 +517,8 @@ def main():
                        else "FP32 FFMA", "ascent": "FP32", "l2": "flushed between timed steps (256 MB write)",
                        "template": "expanded once before timing (resident)",
                        "fp64_rescore_top_k": args.refine,
-                       "autotuned": {"align_lanes_per_start": r["tune"]["align_group"],
+                       "autotuned": {"align_lanes_per_group": r["tune"]["align_group"],
+                                     "align_starts_per_thread": r["tune"]["align_starts_per_thread"],
                                      "gemm_n_tile": r["tune"]["gemm_bn"]},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "breakdown_ms_per_step": {"expand": per_step_exp, "align": per_step_aln, "plan_create_s": r["plan_s"]},

@@ -157,6 +157,19 @@ int bh_expand_noalloc(bh_plan* plan, const float* vols, int B, float* coeffs, vo
 int bh_score_grad(const bh_plan* plan, const float* tmpl, const float* sub, int B,
                   const float* quats, int S, int L, float* score, float* grad, void* stream);
 
+/*
+ * Energy of the cross-correlation coefficients per degree, E_l = sum_{m,m'} |xi^l_{mm'}|^2 for
+ * l = 0..L (FP64 sums, stored as float).  The energy ratio of Fig. 1,
+ * Ratio(L') = sum_{l>L'} E_l / sum_{l<=L} E_l (the caption's sum over m, m' made explicit), picks
+ * high-energy bands for the marching schedule.
+ *   tmpl        device, Nb complex (or n_templates * Nb with tmpl_index)
+ *   sub         device, B * Nb complex
+ *   tmpl_index  device, B ints or NULL
+ *   energy      device, B * (L+1) floats, layout [b][l]
+ */
+int bh_energy(const bh_plan* plan, const float* tmpl, const float* sub, int B, int L, const int* tmpl_index,
+              int n_templates, float* energy, void* stream);
+
 /* ------------------------------------------------------------------ alignment */
 typedef struct {
   int group;              /* lanes cooperating on one start: 0 = autotuned, else 1, 2, 4, 8 or 16 */

@@ -22,7 +22,7 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
-           "bh_align_batch", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_align_batch", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
@@ -226,6 +226,20 @@ def bh_random_starts(seed: int, B: int, S: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ serving
+def bh_energy(plan: Plan, tmpl, sub, L: int, tmpl_index=None, n_templates: int = 0, stream=None):
+    """Per-degree energy E_l (B, L+1) of xi^l and the energy ratio Ratio(L') = sum_{l>L'} E_l / sum E_l."""
+    import torch
+    B = sub.shape[0]
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    e = torch.empty((B, L + 1), dtype=torch.float32, device=sub.device)
+    _check(lib().bh_energy(plan.handle, _ptr(tmpl), _ptr(sub), B, L, _ptr(tmpl_index), n_templates, _ptr(e),
+                           _stream(stream)), "bh_energy")
+    ed = e.double()
+    tail = ed.flip(1).cumsum(1).flip(1)
+    ratio = torch.cat([tail[:, 1:], torch.zeros_like(tail[:, :1])], 1) / ed.sum(1, keepdim=True).clamp_min(1e-300)
+    return e, ratio
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("align_group", ctypes.c_int), ("align_starts_per_thread", ctypes.c_int), ("align_ms", ctypes.c_float),
                 ("gemm_bn", ctypes.c_int), ("expand_ms", ctypes.c_float)]
@@ -261,6 +275,7 @@ def _serve_sigs(L):
         return
     L.bh_random_starts.argtypes = [ctypes.c_uint64, i, i, vp]
     L.bh_autotune.argtypes = [vp, i, i, vp, i, i, ctypes.POINTER(TuneResult)]
+    L.bh_energy.argtypes = [vp, vp, vp, i, i, vp, i, vp, vp]
     L.bh_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeOpts)]
     L.bh_serve_add_template.argtypes = [vp, i, vp, ctypes.POINTER(i)]
     L.bh_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -269,7 +284,7 @@ def _serve_sigs(L):
     L.bh_serve_pause.argtypes = [vp, i]
     L.bh_serve_stats.argtypes = [vp, ctypes.POINTER(ServeCounters)]
     L.bh_serve_destroy.argtypes = [vp]
-    for n in ("bh_random_starts", "bh_autotune", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
+    for n in ("bh_random_starts", "bh_autotune", "bh_energy", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
               "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"):
         getattr(L, n).restype = i
     L._serve_ready = True

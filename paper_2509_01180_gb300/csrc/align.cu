@@ -63,7 +63,6 @@ struct AlignArgs {
   int steps;
   int Lb;  // band of the shared-memory table
   const float* P;       // [orbit table of band Lmax] P_l(m,n) = prod_{j=m+1..l} j(2j-1)/u_j
-  const float2* coef;   // [orbit table of band Lmax] (B_l, g_l) of the rescaled recursion
   const float* lbin;    // [m][m+n] 0.5 log2 C(2m, m+n), row stride 2 kMaxL + 1
   float4* quat_out;
   float* score_out;
@@ -133,113 +132,140 @@ struct Eval {
   float S, gx, gy, gz;
 };
 
-// Score and body-frame gradient of rotation q at band L (FP32), from the orbit table of band Lb >= L.
-// Every lane of a G-group returns the same (bitwise) result.
-template <int G>
-__device__ Eval eval_rotation(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg,
-                              const float2* __restrict__ coef, const float* __restrict__ lbin, int Lmax) {
-  const float w = q.x, x = q.y, y = q.z, z = q.w;
-  const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
-  const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);   // e^{i(alpha+gamma)/2}
-  const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);  // e^{i(alpha-gamma)/2}
-  const float xb = (cb - sb) * (cb + sb);                                             // cos beta
-  const float sinb = 2.f * cb * sb;                                                   // sin beta
-  const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
-  const float lcc = log2f(cbc), lss = log2f(sbc);
-  const float rcs = cbc / sbc, rsc = sbc / cbc;
-  const float2 Es = cconj(es);
-  const float2 EsG = cpow(Es, G), edG = cpow(ed, G);
-  const float2 Ed = cconj(ed);
-  const float2 Ed2 = cmul(Ed, Ed);
-  const float2 Uq = cpow(Es, qg);
-  float2 Wrow = cpow(ed, qg);
-  float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
+// Score and body-frame gradient (FP32) of C rotations at once (C starts of one subtomogram) at band L, from
+// the orbit table of band Lb >= L.  Every lane of a G-group returns the same (bitwise) results.  For C > 1
+// the evaluation is shared: (C starts of one subtomogram): each orbit-step loads the
+// table entry, the per-band constants and the rational coefficient g once and advances C independent
+// recursions, so the shared part of the step is paid once per C starts and every thread carries C
+// independent FMA chains.
+template <int G, int C>
+__device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
+                               const float* __restrict__ lbin, Eval (&out)[C]) {
+  float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
+  float2 es[C], ed[C], R1[C], R2[C], Ed2[C], Uq[C], Wrow[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
+    const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+    es[j] = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+    ed[j] = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+    xb[j] = (cb - sb) * (cb + sb);
+    sinb[j] = 2.f * cb * sb;
+    const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
+    lcc[j] = log2f(cbc);
+    lss[j] = log2f(sbc);
+    rcs[j] = cbc / sbc;
+    rsc[j] = sbc / cbc;
+    const float2 Es = cconj(es[j]);
+    const float2 EsG = cpow(Es, G), edG = cpow(ed[j], G);
+    // along a lane's orbits in a row (n += G) the two phases are geometric with ratios R1, R2
+    R1[j] = cmul(EsG, edG);
+    R2[j] = cmul(EsG, cconj(edG));
+    const float2 Ed = cconj(ed[j]);
+    Ed2[j] = cmul(Ed, Ed);
+    Uq[j] = cpow(Es, qg);
+    Wrow[j] = cpow(ed[j], qg);
+  }
+  float S[C], Sa[C], Sb[C], Sg[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
   for (int m = 0; m <= L; ++m) {
     const int w = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
     const float fm2 = (float)(m * m);
-    float2 U = Uq, W = Wrow;
+    float2 P1[C], P2[C];
+    // row sums: Re z1 + Re z2, Im z1, Im z2, n Im z1, n Im z2, and the beta-derivative part
+    float rS[C], rI1[C], rI2[C], rN1[C], rN2[C], rB[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      P1[j] = cmul(Uq[j], Wrow[j]);
+      P2[j] = cmul(Uq[j], cconj(Wrow[j]));
+      rS[j] = rI1[j] = rI2[j] = rN1[j] = rN2[j] = rB[j] = 0.f;
+    }
     for (int n = qg - m; n <= m; n += G) {
-      // seed at l = m: d = sg 2^lb c^(m+n) s^(m-n), c = cos(beta/2), s = sin(beta/2) (both clamped to
-      // >= 1e-30, which changes no value above the FP32 underflow), and its beta-derivative
-      // d' = d ((m-n) c/s - (m+n) s/c) / 2
       const float lb = __ldg(lbin + m * kBinStride + m + n);
-      const float fa = (float)(m + n), fd = (float)(m - n);
-      float d = exp2f(lb + fa * lcc + fd * lss);
-      d = ((m - n) & 1) ? -d : d;
-      const float dp = 0.5f * d * (fd * rcs - fa * rsc);
+      const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
+      const bool odd = (m - n) & 1;
+      float e1[C], e2[C], p1[C], p2[C];
+      float a1r[C], a1i[C], a2r[C], a2i[C], b1r[C], b1i[C], b2r[C], b2i[C];
       const float4* ep = rowp + (n + m);
       float4 xv = *ep;
-      float a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
-      float b1r = dp * xv.x, b1i = dp * xv.y, b2r = dp * xv.z, b2i = dp * xv.w;
-      float e1 = d, e2 = 0.f, p1 = dp, p2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        float d = exp2f(lb + fa * lcc[j] + fd * lss[j]);
+        d = odd ? -d : d;
+        const float dp = 0.5f * d * (fd * rcs[j] - fa * rsc[j]);
+        a1r[j] = d * xv.x; a1i[j] = d * xv.y; a2r[j] = d * xv.z; a2i[j] = d * xv.w;
+        b1r[j] = dp * xv.x; b1i[j] = dp * xv.y; b2r[j] = dp * xv.z; b2i[j] = dp * xv.w;
+        e1[j] = d; e2[j] = 0.f; p1[j] = dp; p2[j] = 0.f;
+      }
       const float mn = (float)(m * n), fn2 = (float)(n * n);
-      int l = m + 1;
-      // one step: t = cos(beta) - m n / (l(l-1)),  g = ((l-1)^2 - m^2)((l-1)^2 - n^2) / ((l-1)^2 (2l-1)(2l-3))
-#define BH_ORBIT_STEP(E_NEW, P_NEW, E1, E2, P1, P2, K, X)                   \
-  {                                                                        \
-    const float t_ = fmaf(-mn, (K).x, xb);                                 \
-    const float g_ = ((K).z - fm2) * ((K).z - fn2) * (K).y;                \
-    E_NEW = fmaf(t_, E1, -g_ * E2);                                        \
-    P_NEW = fmaf(t_, P1, -fmaf(sinb, E1, g_ * P2));                        \
-    a1r = fmaf(E_NEW, (X).x, a1r);                                         \
-    a1i = fmaf(E_NEW, (X).y, a1i);                                         \
-    a2r = fmaf(E_NEW, (X).z, a2r);                                         \
-    a2i = fmaf(E_NEW, (X).w, a2i);                                         \
-    b1r = fmaf(P_NEW, (X).x, b1r);                                         \
-    b1i = fmaf(P_NEW, (X).y, b1i);                                         \
-    b2r = fmaf(P_NEW, (X).z, b2r);                                         \
-    b2i = fmaf(P_NEW, (X).w, b2i);                                         \
-  }
-      for (; l + 1 <= L; l += 2) {
+      for (int l = m + 1; l <= L; ++l) {
         ep += w;
-        const float4 k0 = c_ecoef[l];
-        const float4 x0 = *ep;
-        ep += w;
-        const float4 k1 = c_ecoef[l + 1];
-        const float4 x1 = *ep;
-        float ea, pa, eb, pb;
-        BH_ORBIT_STEP(ea, pa, e1, e2, p1, p2, k0, x0);
-        BH_ORBIT_STEP(eb, pb, ea, e1, pa, p1, k1, x1);
-        e2 = ea;
-        e1 = eb;
-        p2 = pa;
-        p1 = pb;
+        const float4 k = c_ecoef[l];
+        xv = *ep;
+        const float g = (k.z - fm2) * (k.z - fn2) * k.y;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const float t = fmaf(-mn, k.x, xb[j]);
+          const float en = fmaf(t, e1[j], -g * e2[j]);
+          const float pn = fmaf(t, p1[j], -fmaf(sinb[j], e1[j], g * p2[j]));
+          e2[j] = e1[j]; e1[j] = en; p2[j] = p1[j]; p1[j] = pn;
+          a1r[j] = fmaf(en, xv.x, a1r[j]); a1i[j] = fmaf(en, xv.y, a1i[j]);
+          a2r[j] = fmaf(en, xv.z, a2r[j]); a2i[j] = fmaf(en, xv.w, a2i[j]);
+          b1r[j] = fmaf(pn, xv.x, b1r[j]); b1i[j] = fmaf(pn, xv.y, b1i[j]);
+          b2r[j] = fmaf(pn, xv.z, b2r[j]); b2i[j] = fmaf(pn, xv.w, b2i[j]);
+        }
       }
-      if (l <= L) {
-        ep += w;
-        const float4 k0 = c_ecoef[l];
-        const float4 x0 = *ep;
-        float ea, pa;
-        BH_ORBIT_STEP(ea, pa, e1, e2, p1, p2, k0, x0);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float z1r = P1[j].x * a1r[j] - P1[j].y * a1i[j], z1i = P1[j].x * a1i[j] + P1[j].y * a1r[j];
+        const float z2r = P2[j].x * a2r[j] - P2[j].y * a2i[j], z2i = P2[j].x * a2i[j] + P2[j].y * a2r[j];
+        rS[j] += z1r + z2r;
+        rI1[j] += z1i;
+        rI2[j] += z2i;
+        rN1[j] = fmaf(fn, z1i, rN1[j]);
+        rN2[j] = fmaf(fn, z2i, rN2[j]);
+        rB[j] += (P1[j].x * b1r[j] - P1[j].y * b1i[j]) + (P2[j].x * b2r[j] - P2[j].y * b2i[j]);
+        P1[j] = cmul(P1[j], R1[j]);
+        P2[j] = cmul(P2[j], R2[j]);
       }
-#undef BH_ORBIT_STEP
-      const float2 P1 = cmul(U, W), P2 = cmul(U, cconj(W));
-      const float2 z1 = cmul(P1, make_float2(a1r, a1i)), z2 = cmul(P2, make_float2(a2r, a2i));
-      S += z1.x + z2.x;
-      Sa += (float)m * z1.y + (float)n * z2.y;
-      Sg += (float)n * z1.y + (float)m * z2.y;
-      Sb += (P1.x * b1r - P1.y * b1i) + (P2.x * b2r - P2.y * b2i);
-      U = cmul(U, EsG);
-      W = cmul(W, edG);
     }
-    Wrow = cmul(Wrow, Ed2);
+    const float fm = (float)m;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      S[j] += rS[j];
+      Sa[j] += fm * rI1[j] + rN2[j];
+      Sg[j] += rN1[j] + fm * rI2[j];
+      Sb[j] += rB[j];
+      Wrow[j] = cmul(Wrow[j], Ed2[j]);
+    }
   }
 #pragma unroll
-  for (int o = 1; o < G; o <<= 1) {
-    S += __shfl_xor_sync(0xffffffffu, S, o);
-    Sa += __shfl_xor_sync(0xffffffffu, Sa, o);
-    Sb += __shfl_xor_sync(0xffffffffu, Sb, o);
-    Sg += __shfl_xor_sync(0xffffffffu, Sg, o);
+  for (int j = 0; j < C; ++j) {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      S[j] += __shfl_xor_sync(0xffffffffu, S[j], o);
+      Sa[j] += __shfl_xor_sync(0xffffffffu, Sa[j], o);
+      Sb[j] += __shfl_xor_sync(0xffffffffu, Sb[j], o);
+      Sg[j] += __shfl_xor_sync(0xffffffffu, Sg[j], o);
+    }
+    const float2 eg = cmul(es[j], cconj(ed[j]));
+    const float Q = (sinb[j] > 1e-30f) ? (xb[j] * Sg[j] - Sa[j]) / sinb[j] : 0.f;
+    out[j].S = S[j];
+    out[j].gx = Sb[j] * eg.y + Q * eg.x;
+    out[j].gy = Sb[j] * eg.x - Q * eg.y;
+    out[j].gz = Sg[j];
   }
-  const float2 eg = cmul(es, cconj(ed));  // e^{i gamma}
-  const float Q = (sinb > 1e-30f) ? (xb * Sg - Sa) / sinb : 0.f;
-  Eval r;
-  r.S = S;
-  r.gx = Sb * eg.y + Q * eg.x;
-  r.gy = Sb * eg.x - Q * eg.y;
-  r.gz = Sg;
-  return r;
+}
+
+template <int G>
+__device__ __forceinline__ Eval eval_one(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg,
+                                         const float* __restrict__ lbin) {
+  const float4 qq[1] = {q};
+  Eval e[1];
+  eval_rotations<G, 1>(tab, Lb, L, qq, qg, lbin, e);
+  return e[0];
 }
 
 __device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p) {
@@ -273,7 +299,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align(const AlignArgs a)
     const int L = a.stages[st];
     const float hmax = 3.14159265358979f / (float)L;
     float h = 0.5f * hmax;
-    cur = eval_rotation<G>(smem_tab, a.Lb, L, q, qg, a.coef, a.lbin, a.lay.Lmax);
+    cur = eval_one<G>(smem_tab, a.Lb, L, q, qg, a.lbin);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -282,7 +308,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align(const AlignArgs a)
       sincosf(stop ? 0.f : 0.5f * h, &sh, &ch);
       const float4 dq = make_float4(ch, sh * cur.gx * inv, sh * cur.gy * inv, sh * cur.gz * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const Eval tr = eval_rotation<G>(smem_tab, a.Lb, L, qt, qg, a.coef, a.lbin, a.lay.Lmax);
+      const Eval tr = eval_one<G>(smem_tab, a.Lb, L, qt, qg, a.lbin);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -325,7 +351,7 @@ __global__ void __launch_bounds__(512, 1) k_score(const AlignArgs a, int L) {
               blockDim.x);
   __syncthreads();
   const float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
-  const Eval r = eval_rotation<G>(smem_tab, a.Lb, L, q, qg, a.coef, a.lbin, a.lay.Lmax);
+  const Eval r = eval_one<G>(smem_tab, a.Lb, L, q, qg, a.lbin);
   if (active && qg == 0) {
     a.score_out[(size_t)p * a.S + s] = r.S;
     if (a.grad_out) {
@@ -334,118 +360,6 @@ __global__ void __launch_bounds__(512, 1) k_score(const AlignArgs a, int L) {
       g[1] = r.gy;
       g[2] = r.gz;
     }
-  }
-}
-
-// ---------------------------------------------------------------------------- C starts per thread
-// The same evaluation for C rotations at once (C starts of one subtomogram): each orbit-step loads the
-// table entry, the per-band constants and the rational coefficient g once and advances C independent
-// recursions, so the shared part of the step is paid once per C starts and every thread carries C
-// independent FMA chains.
-template <int G, int C>
-__device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
-                               const float* __restrict__ lbin, Eval (&out)[C]) {
-  float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
-  float2 es[C], ed[C], EsG[C], edG[C], Ed2[C], Uq[C], Wrow[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
-    const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
-    es[j] = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
-    ed[j] = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
-    xb[j] = (cb - sb) * (cb + sb);
-    sinb[j] = 2.f * cb * sb;
-    const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
-    lcc[j] = log2f(cbc);
-    lss[j] = log2f(sbc);
-    rcs[j] = cbc / sbc;
-    rsc[j] = sbc / cbc;
-    const float2 Es = cconj(es[j]);
-    EsG[j] = cpow(Es, G);
-    edG[j] = cpow(ed[j], G);
-    const float2 Ed = cconj(ed[j]);
-    Ed2[j] = cmul(Ed, Ed);
-    Uq[j] = cpow(Es, qg);
-    Wrow[j] = cpow(ed[j], qg);
-  }
-  float S[C], Sa[C], Sb[C], Sg[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
-  for (int m = 0; m <= L; ++m) {
-    const int w = 2 * m + 1;
-    const float4* rowp = tab + tab_base(m, Lb);
-    const float fm2 = (float)(m * m);
-    float2 U[C], W[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      U[j] = Uq[j];
-      W[j] = Wrow[j];
-    }
-    for (int n = qg - m; n <= m; n += G) {
-      const float lb = __ldg(lbin + m * kBinStride + m + n);
-      const float fa = (float)(m + n), fd = (float)(m - n);
-      const bool odd = (m - n) & 1;
-      float e1[C], e2[C], p1[C], p2[C];
-      float a1r[C], a1i[C], a2r[C], a2i[C], b1r[C], b1i[C], b2r[C], b2i[C];
-      const float4* ep = rowp + (n + m);
-      float4 xv = *ep;
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        float d = exp2f(lb + fa * lcc[j] + fd * lss[j]);
-        d = odd ? -d : d;
-        const float dp = 0.5f * d * (fd * rcs[j] - fa * rsc[j]);
-        a1r[j] = d * xv.x; a1i[j] = d * xv.y; a2r[j] = d * xv.z; a2i[j] = d * xv.w;
-        b1r[j] = dp * xv.x; b1i[j] = dp * xv.y; b2r[j] = dp * xv.z; b2i[j] = dp * xv.w;
-        e1[j] = d; e2[j] = 0.f; p1[j] = dp; p2[j] = 0.f;
-      }
-      const float mn = (float)(m * n), fn2 = (float)(n * n);
-      for (int l = m + 1; l <= L; ++l) {
-        ep += w;
-        const float4 k = c_ecoef[l];
-        xv = *ep;
-        const float g = (k.z - fm2) * (k.z - fn2) * k.y;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const float t = fmaf(-mn, k.x, xb[j]);
-          const float en = fmaf(t, e1[j], -g * e2[j]);
-          const float pn = fmaf(t, p1[j], -fmaf(sinb[j], e1[j], g * p2[j]));
-          e2[j] = e1[j]; e1[j] = en; p2[j] = p1[j]; p1[j] = pn;
-          a1r[j] = fmaf(en, xv.x, a1r[j]); a1i[j] = fmaf(en, xv.y, a1i[j]);
-          a2r[j] = fmaf(en, xv.z, a2r[j]); a2i[j] = fmaf(en, xv.w, a2i[j]);
-          b1r[j] = fmaf(pn, xv.x, b1r[j]); b1i[j] = fmaf(pn, xv.y, b1i[j]);
-          b2r[j] = fmaf(pn, xv.z, b2r[j]); b2i[j] = fmaf(pn, xv.w, b2i[j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const float2 P1 = cmul(U[j], W[j]), P2 = cmul(U[j], cconj(W[j]));
-        const float2 z1 = cmul(P1, make_float2(a1r[j], a1i[j])), z2 = cmul(P2, make_float2(a2r[j], a2i[j]));
-        S[j] += z1.x + z2.x;
-        Sa[j] += (float)m * z1.y + (float)n * z2.y;
-        Sg[j] += (float)n * z1.y + (float)m * z2.y;
-        Sb[j] += (P1.x * b1r[j] - P1.y * b1i[j]) + (P2.x * b2r[j] - P2.y * b2i[j]);
-        U[j] = cmul(U[j], EsG[j]);
-        W[j] = cmul(W[j], edG[j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < C; ++j) Wrow[j] = cmul(Wrow[j], Ed2[j]);
-  }
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) {
-      S[j] += __shfl_xor_sync(0xffffffffu, S[j], o);
-      Sa[j] += __shfl_xor_sync(0xffffffffu, Sa[j], o);
-      Sb[j] += __shfl_xor_sync(0xffffffffu, Sb[j], o);
-      Sg[j] += __shfl_xor_sync(0xffffffffu, Sg[j], o);
-    }
-    const float2 eg = cmul(es[j], cconj(ed[j]));
-    const float Q = (sinb[j] > 1e-30f) ? (xb[j] * Sg[j] - Sa[j]) / sinb[j] : 0.f;
-    out[j].S = S[j];
-    out[j].gx = Sb[j] * eg.y + Q * eg.x;
-    out[j].gy = Sb[j] * eg.x - Q * eg.y;
-    out[j].gz = Sg[j];
   }
 }
 
@@ -525,6 +439,42 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs 
     a.quat_out[p] = sQ[best];
     a.score_out[p] = sS[best];
   }
+}
+
+// ---------------------------------------------------------------------------- energy per degree
+// E_l = sum_{m,m'} |xi^l_{mm'}|^2 (Fig. 1's energy ratio is built from these): one CTA per
+// (subtomogram, degree), threads over (m, m') pairs, FP64 block sum.
+__global__ void __launch_bounds__(256) k_energy(Layout lay, const float2* __restrict__ tmpl,
+                                                const int* __restrict__ tmpl_index, int n_templates,
+                                                const float2* __restrict__ sub, int L, float* __restrict__ energy) {
+  const int p = blockIdx.x, l = blockIdx.y;
+  const float2* t = tmpl;
+  if (tmpl_index) {
+    int ti = tmpl_index[p];
+    ti = ti < 0 ? 0 : (ti >= n_templates ? n_templates - 1 : ti);
+    t += (size_t)ti * lay.Nb;
+  }
+  const float2* f = sub + (size_t)p * lay.Nb;
+  const int w = 2 * l + 1, K = lay.K[l], off = lay.off[l];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < w * w; i += blockDim.x) {
+    const int m = i / w, n = i % w;
+    double xr = 0.0, xi = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const float2 a = __ldg(t + off + k * w + m), b = __ldg(f + off + k * w + n);
+      xr += (double)a.x * b.x + (double)a.y * b.y;
+      xi += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    acc += xr * xr + xi * xi;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) energy[(size_t)p * (L + 1) + l] = (float)red[0];
 }
 
 // ---------------------------------------------------------------------------- FP64 re-scoring
@@ -827,7 +777,6 @@ extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* s
   a.S = S;
   a.Lb = L;
   a.P = p->d_P;
-  a.coef = p->d_coef;
   a.lbin = p->d_lbin;
   a.score_out = score;
   a.grad_out = grad;
@@ -861,7 +810,6 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   a.steps = steps;
   a.Lb = stages[nstages - 1];
   a.P = p->d_P;
-  a.coef = p->d_coef;
   a.lbin = p->d_lbin;
   a.quat_out = reinterpret_cast<float4*>(quat_out);
   a.score_out = score_out;
@@ -1012,5 +960,22 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
     out->gemm_bn = best_bn;
     out->expand_ms = best_ems;
   }
+  return BH_OK;
+}
+
+extern "C" int bh_energy(const bh_plan* p, const float* tmpl, const float* sub, int B, int L, const int* tmpl_index,
+                         int n_templates, float* energy, void* stream) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 0 || L < 0 || L > p->Lmax) return fail(BH_ERR_ARG, "B=%d L=%d", B, L);
+  if (B == 0) return BH_OK;
+  if (!tmpl || !sub || !energy) return fail(BH_ERR_ARG, "NULL array");
+  if (tmpl_index && n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d", n_templates);
+  if (B > 65535 * 1024) return fail(BH_ERR_ARG, "B=%d too large", B);
+  dim3 grid(B, L + 1);
+  k_energy<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(p->layout, reinterpret_cast<const float2*>(tmpl),
+                                                                 tmpl_index, n_templates,
+                                                                 reinterpret_cast<const float2*>(sub), L, energy);
+  BH_CHECK_LAUNCH();
   return BH_OK;
 }

@@ -75,10 +75,9 @@ struct bh_plan {
   float* d_C = nullptr;             // [ksplit_max][M_cap][Nb_pad] real GEMM output (per K split)
   int* d_err = nullptr;             // device status word written by bounded waits
   float* d_P = nullptr;             // orbit-table scale P_l(m,n), layout [m][l][n] for l <= Lmax
-  float2* d_coef = nullptr;         // (B_l, g_l) of the rescaled d recursion, same layout
   float* d_lbin = nullptr;          // 0.5 log2 C(2m, m+n) at [m][m+n], row stride 2 kMaxL + 1
-  double2* d_coef64 = nullptr;      // FP64 copies of the two tables above (FP64 re-scoring)
-  double* d_lbin64 = nullptr;
+  double2* d_coef64 = nullptr;      // (B_l, g_l) of the rescaled d recursion in FP64, same layout (FP64 re-scoring)
+  double* d_lbin64 = nullptr;       // FP64 copy of d_lbin
   int gemm_bn = 128;                // N tile of the tensor-core GEMM
   int num_sms = 152;                // SMs of the device (split-K sizing)
   int ksplit_max = 1;               // K splits the GEMM-output scratch holds

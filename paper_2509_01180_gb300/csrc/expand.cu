@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, c
   __shared__ __align__(16) float As[SG_BK][SG_BM + SG_PAD];
   __shared__ __align__(16) float Bs[SG_BK][SG_BN + SG_PAD];
   const int tid = threadIdx.x;
-  const int m0 = blockIdx.y * SG_BM, n0 = blockIdx.x * SG_BN;
+  const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;  // M fastest: CTAs in flight share table panels
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: rows lr and lr+64, k columns lk..lk+3
   const int tx = tid & 15, ty = tid >> 4;
   const float* Ap0 = A + (size_t)(m0 + lr) * K + kbeg + lk;
@@ -291,7 +291,9 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ uint32_t tmem_base_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * PCfg::BM, n0 = blockIdx.x * PBN;
+  // M tiles vary fastest across the grid, so the CTAs in flight share table (B) panels, the operand
+  // larger than L2, while the gathered volumes (A) stay L2-resident
+  const int m0 = blockIdx.x * PCfg::BM, n0 = blockIdx.y * PBN;
   const int nchunks = (num_kb + KCHUNK - 1) / KCHUNK;
   auto sA_hi = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES; };
   auto sA_lo = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES + PCfg::A_BYTES; };
@@ -510,7 +512,7 @@ static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
   const size_t stride = (size_t)p->M_cap * p->Nb_pad;
   if (p->mode == BH_MODE_FP32) {
     const int k_split = round_up((p->V_pad + splits - 1) / splits, SG_BK);
-    dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM, (p->V_pad + k_split - 1) / k_split);  // every split has K work
+    dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN, (p->V_pad + k_split - 1) / k_split);  // every split has K work
     k_sgemm_nt<<<grid, 256, 0, stream>>>(p->d_X32, p->d_T32, p->d_C, Mp, p->Nb_pad, p->V_pad, k_split, stride);
     BH_CHECK_LAUNCH();
     return BH_OK;
@@ -523,7 +525,7 @@ static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
                                      (int)PCfg::SMEM));
     attr = true;
   }
-  dim3 grid(p->Nb_pad / PBN, Mp / kGemmBM, (num_kb + kb_split - 1) / kb_split);
+  dim3 grid(Mp / kGemmBM, p->Nb_pad / PBN, (num_kb + kb_split - 1) / kb_split);
   k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
                                                       p->Nb_pad, num_kb, kb_split, stride, p->d_err);
   BH_CHECK_LAUNCH();
@@ -556,13 +558,13 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
     k_gather<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
     BH_CHECK_LAUNCH();
     if (p->mode == BH_MODE_FP32) {
-      dim3 grid(p->Nb_pad / SG_BN, Mp / SG_BM);
+      dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN);
       k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, scratch_c, Mp, p->Nb_pad, p->V_pad, p->V_pad, 0);
     } else {
       const int num_kb = p->V_pad / kGemmBK;
       BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_promoted, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)PCfg::SMEM));
-      dim3 grid(p->Nb_pad / PBN, Mp / kGemmBM);
+      dim3 grid(Mp / kGemmBM, p->Nb_pad / PBN);
       k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c, p->Nb_pad,
                                                           num_kb, num_kb, 0, p->d_err);
     }

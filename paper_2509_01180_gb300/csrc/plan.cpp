@@ -207,7 +207,6 @@ static void free_plan(bh_plan* p) {
   cudaFree(p->d_C);
   cudaFree(p->d_err);
   cudaFree(p->d_P);
-  cudaFree(p->d_coef);
   cudaFree(p->d_lbin);
   cudaFree(p->d_coef64);
   cudaFree(p->d_lbin64);
@@ -422,9 +421,7 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     PLAN_TRY(cuda_ok(cudaMemcpy(p->d_P, P.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice), "upload P"));
     // coefficients of the rescaled recursion e^l = (cos beta - B_l) e^{l-1} - g_l e^{l-2}:
     //   B_l = m n / (l (l-1)),  g_l = ((l-1)^2 - m^2)((l-1)^2 - n^2) / ((l-1)^2 (2l-1)(2l-3))  (0 at l < 2)
-    std::vector<float2> co;
     std::vector<double2> co64;
-    co.reserve(P.size());
     co64.reserve(P.size());
     for (int m = 0; m <= p->Lmax; ++m)
       for (int l = m; l <= p->Lmax; ++l)
@@ -435,11 +432,8 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
             B = (double)m * n / ((double)l * (l - 1));
             g = (a - (double)m * m) * (a - (double)n * n) / (a * (2.0 * l - 1.0) * (2.0 * l - 3.0));
           }
-          co.push_back(make_float2((float)B, (float)g));
           co64.push_back(make_double2(B, g));
         }
-    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_coef, sizeof(float2) * co.size()), "cudaMalloc coef"));
-    PLAN_TRY(cuda_ok(cudaMemcpy(p->d_coef, co.data(), sizeof(float2) * co.size(), cudaMemcpyHostToDevice), "upload coef"));
     // 0.5 log2 C(2m, j), j = m + n
     const int stride = 2 * kMaxL + 1;
     std::vector<float> lb((size_t)(kMaxL + 1) * stride, 0.f);

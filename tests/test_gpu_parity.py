@@ -326,3 +326,19 @@ def test_expand_64_box_matches_oracle(dev, mode):
     ref = ball.expand(basis_for(64, 32), vols.astype(np.float64))
     for b in range(2):
         assert rel_l2(got[b], ref[b]) < 3e-5, (b, rel_l2(got[b], ref[b]))
+
+
+def test_energy_ratio_matches_oracle(dev):
+    """Fig. 1's energy per degree and energy ratio (sums over m, m' made explicit) vs the oracle."""
+    w = synth.make_workload("batch32", count=2)
+    Bs = basis_for(32, 16)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    F = ball.expand(Bs, w.vols.astype(np.float64))
+    p = plan_for(32, 16, bh.BH_MODE_FP32)
+    e, ratio = bh.bh_energy(p, to_f32(t).to(dev), to_f32(F).to(dev), 16)
+    e, ratio = e.cpu().numpy(), ratio.cpu().numpy()
+    for b in range(2):
+        xi = align.build_xi(Bs, t, F[b], 16)
+        ref_e = np.array([np.sum(np.abs(x) ** 2) for x in xi])
+        assert np.allclose(e[b], ref_e, rtol=1e-4, atol=1e-12 * ref_e.max())
+        assert np.allclose(ratio[b], align.energy_ratio(xi), atol=1e-5)
