@@ -200,23 +200,43 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
         e1[j] = d; e2[j] = 0.f; p1[j] = dp; p2[j] = 0.f;
       }
       const float mn = (float)(m * n), fn2 = (float)(n * n);
-      for (int l = m + 1; l <= L; ++l) {
-        ep += w;
-        const float4 k = c_ecoef[l];
-        xv = *ep;
-        const float g = (k.z - fm2) * (k.z - fn2) * k.y;
+      // one step of band l for start j: (E1, E2, P1, P2) -> (EN, PN), accumulate against X
+#define BH_STEP(J, EN, PN, E1, E2, P1, P2, K, G_, X)                                \
+  {                                                                               \
+    const float t_ = fmaf(-mn, (K).x, xb[J]);                                     \
+    EN = fmaf(t_, E1, -(G_) * E2);                                                \
+    PN = fmaf(t_, P1, -fmaf(sinb[J], E1, (G_) * P2));                             \
+    a1r[J] = fmaf(EN, (X).x, a1r[J]); a1i[J] = fmaf(EN, (X).y, a1i[J]);           \
+    a2r[J] = fmaf(EN, (X).z, a2r[J]); a2i[J] = fmaf(EN, (X).w, a2i[J]);           \
+    b1r[J] = fmaf(PN, (X).x, b1r[J]); b1i[J] = fmaf(PN, (X).y, b1i[J]);           \
+    b2r[J] = fmaf(PN, (X).z, b2r[J]); b2i[J] = fmaf(PN, (X).w, b2i[J]);           \
+  }
+      int l = m + 1;
+      for (; l + 1 <= L; l += 2) {  // two bands per iteration: no register rotation, half the loop overhead
+        const float4 k0 = c_ecoef[l], k1 = c_ecoef[l + 1];
+        const float4 x0 = ep[w], x1 = ep[2 * w];
+        ep += 2 * w;
+        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
+        const float g1 = (k1.z - fm2) * (k1.z - fn2) * k1.y;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-          const float t = fmaf(-mn, k.x, xb[j]);
-          const float en = fmaf(t, e1[j], -g * e2[j]);
-          const float pn = fmaf(t, p1[j], -fmaf(sinb[j], e1[j], g * p2[j]));
-          e2[j] = e1[j]; e1[j] = en; p2[j] = p1[j]; p1[j] = pn;
-          a1r[j] = fmaf(en, xv.x, a1r[j]); a1i[j] = fmaf(en, xv.y, a1i[j]);
-          a2r[j] = fmaf(en, xv.z, a2r[j]); a2i[j] = fmaf(en, xv.w, a2i[j]);
-          b1r[j] = fmaf(pn, xv.x, b1r[j]); b1i[j] = fmaf(pn, xv.y, b1i[j]);
-          b2r[j] = fmaf(pn, xv.z, b2r[j]); b2i[j] = fmaf(pn, xv.w, b2i[j]);
+          float ea, pa, eb, pb;
+          BH_STEP(j, ea, pa, e1[j], e2[j], p1[j], p2[j], k0, g0, x0);
+          BH_STEP(j, eb, pb, ea, e1[j], pa, p1[j], k1, g1, x1);
+          e2[j] = ea; e1[j] = eb; p2[j] = pa; p1[j] = pb;
         }
       }
+      if (l <= L) {
+        const float4 k0 = c_ecoef[l];
+        const float4 x0 = ep[w];
+        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          float ea, pa;
+          BH_STEP(j, ea, pa, e1[j], e2[j], p1[j], p2[j], k0, g0, x0);
+        }
+      }
+#undef BH_STEP
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         const float z1r = P1[j].x * a1r[j] - P1[j].y * a1i[j], z1i = P1[j].x * a1i[j] + P1[j].y * a1r[j];
@@ -275,9 +295,10 @@ __device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p)
   return a.tmpl + (size_t)t * a.lay.Nb;
 }
 
-// Minimum resident CTAs per SM requested from the compiler for a block of NT threads: enough that the
-// register budget allows >= 7 small CTAs (shared memory allows 7 orbit tables of band 16 per SM).
-__host__ __device__ constexpr int min_blocks(int NT) { return NT <= 64 ? 8 : NT <= 128 ? 7 : NT <= 256 ? 3 : 1; }
+// Minimum resident CTAs per SM requested from the compiler for a block of NT threads.  Small blocks (one
+// or two warps) keep 8 resident CTAs (shared memory holds 7 orbit tables of band 16); larger blocks are
+// used when the table is large and few CTAs fit, so they get at least 128 registers per thread.
+__host__ __device__ constexpr int min_blocks(int NT) { return NT <= 64 ? 8 : NT <= 128 ? 4 : NT <= 256 ? 2 : 1; }
 
 // Multi-start marching ascent; one CTA per subtomogram, blockDim = NT = roundup(S*G, 32).
 template <int G, int NT>

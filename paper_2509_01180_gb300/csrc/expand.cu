@@ -234,6 +234,19 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory matrix descriptor of a K-major tile with 128-byte rows and the 128-byte swizzle:
 // start address >> 4 at bits [0,14), leading byte offset (unused for this layout) = 16 B at [16,30),
 // stride byte offset = 1024 B (one 8-row swizzle atom) at [32,46), descriptor version 1 at [46,48),
@@ -261,18 +274,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Tensor-core GEMM with FP32 promotion of the accumulator.  Additions into the tcgen05 accumulator in
 // TMEM truncate, so their error grows with the number of accumulate steps (3 K/16 per output, ~2.6e4 at
 // a 64^3 box); here every KCHUNK K-blocks the MMA issuer switches to the other of two TMEM accumulators
-// (started afresh), and the four epilogue warps add each finished chunk into an FP32 running sum kept in
-// shared memory (one row per thread, rows padded by one float), then hand the TMEM buffer back.
-//   warp 4 lane 0: TMA producer (2-stage ring of A hi/lo and B hi/lo tiles, 128-byte swizzle)
+// (started afresh), and the four epilogue warps add each finished chunk into an FP32 running sum held in
+// a third TMEM region (tcgen05.ld, FP32 add in registers, tcgen05.st), then hand the buffer back.
+//   warp 4 lane 0: TMA producer (3-stage ring of A hi/lo and B hi/lo tiles, 128-byte swizzle)
 //   warp 5 lane 0: MMA issuer (three tcgen05.mma per 16-wide K step: hi*hi, hi*lo, lo*hi)
 //   warps 0-3:     epilogue (warp w owns TMEM lanes and tile rows 32w..32w+31)
-constexpr int PBN = 128, PST = 2, KCHUNK = 16;
+constexpr int PBN = 128, PST = 3, KCHUNK = 16;
 struct PCfg {
   static constexpr int BM = kGemmBM, BK = kGemmBK;
   static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = PBN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int ROW = PBN + 1;  // padded running-sum row (floats)
-  static constexpr size_t SMEM = (size_t)PST * STAGE_BYTES + (size_t)BM * ROW * 4 + 1024;
+  static constexpr size_t SMEM = (size_t)PST * STAGE_BYTES + 1024;
+  // TMEM columns: accumulators [0, PBN) and [PBN, 2 PBN), FP32 running sum [2 PBN, 3 PBN)
+  static constexpr uint32_t TMEM_COLS = 512;
+  static constexpr uint32_t SUM_COL = 2 * PBN;
 };
 
 __global__ void __launch_bounds__(192, 1)
@@ -286,7 +301,6 @@ __global__ void __launch_bounds__(192, 1)
   C += (size_t)blockIdx.z * split_stride;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* acc = reinterpret_cast<float*>(smem + (size_t)PST * PCfg::STAGE_BYTES);
   __shared__ __align__(8) uint64_t full_bar[PST], empty_bar[PST], accf_bar[2], acce_bar[2];
   __shared__ uint32_t tmem_base_sh;
 
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(192, 1)
     mbar_fence_init();
   }
   if (warp == 0) {
-    tmem_alloc(&tmem_base_sh, 2 * PBN);
+    tmem_alloc(&tmem_base_sh, PCfg::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -373,37 +387,44 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // ---------------- epilogue warps 0-3: promote every chunk into the FP32 running sum
+    // ---------------- epilogue warps 0-3: promote every chunk into the FP32 running sum (TMEM)
     const int row = warp * 32 + lane;
-    float* arow = acc + (size_t)row * PCfg::ROW;
-    for (int j = 0; j < PBN; ++j) arow[j] = 0.f;
+    const uint32_t lanes = (uint32_t)(warp * 32) << 16;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int buf = c & 1, use = c >> 1;
       if (ok) ok = mbar_wait(&accf_bar[buf], (uint32_t)(use & 1), err, 115);
       ok = __all_sync(0xffffffffu, ok);
       tc_fence_after();
+      const bool last = (c + 1 == nchunks);
 #pragma unroll 1
       for (int cc = 0; cc < PBN / 32; ++cc) {
-        uint32_t r[32];
-        tmem_ld_32x32b_x32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * PBN + cc * 32), r);
+        uint32_t r[32], t[32];
+        tmem_ld_32x32b_x32(tbase + lanes + (uint32_t)(buf * PBN + cc * 32), r);
+        if (c > 0) tmem_ld_32x32b_x32(tbase + lanes + PCfg::SUM_COL + (uint32_t)(cc * 32), t);
         tmem_ld_wait();
+        if (c > 0) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) arow[cc * 32 + i] += __uint_as_float(r[i]);
+          for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(__uint_as_float(r[i]) + __uint_as_float(t[i]));
+        }
+        if (!last) {
+          tmem_st_32x32b_x32(tbase + lanes + PCfg::SUM_COL + (uint32_t)(cc * 32), r);
+        } else if (ok) {
+          float4* dst = reinterpret_cast<float4*>(C + (size_t)(m0 + row) * ldc + n0 + cc * 32);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            dst[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]), __uint_as_float(r[4 * i + 2]),
+                                 __uint_as_float(r[4 * i + 3]));
+        }
       }
+      tmem_st_wait();
       tc_fence_before();
       mbar_arrive(&acce_bar[buf]);
-    }
-    if (ok) {
-      float* crow = C + (size_t)(m0 + row) * ldc + n0;
-#pragma unroll 4
-      for (int j = 0; j < PBN; j += 4)
-        *reinterpret_cast<float4*>(crow + j) = make_float4(arow[j], arow[j + 1], arow[j + 2], arow[j + 3]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, 2 * PBN);
+  if (warp == 0) tmem_dealloc(tbase, PCfg::TMEM_COLS);
 }
 
 }  // namespace
