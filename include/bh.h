@@ -206,6 +206,28 @@ int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int
                    const float* starts, int S, const int* stages, int nstages, int steps,
                    float* quat_out, float* score_out, const bh_align_opts* opts, void* stream);
 
+/* ------------------------------------------------------------------ shift search */
+/*
+ * Rotational matching over a grid of shifts (Eq. 1 over R^3 x SO(3); Sec. II-C: maximise Eq. 2 for a
+ * shift s and repeat over a grid of shifts).  For every subtomogram f and integer-voxel shift s_j,
+ * f_s(x) = f(x + s_j) (zero outside the box) is expanded, Eq. 2 with xi^s is maximised by the marching
+ * ascent from the same starts, and the (shift, rotation) with the largest final score is returned.
+ *   vols        device, B * N^3 floats
+ *   shifts      host, nshift * 3 ints (sx, sy, sz) in voxels, each in (-N, N); nshift in 1..4096
+ *   starts      device, B * S * 4 floats (used for every shift)
+ *   workspace   device, >= bh_align_shifts_workspace(plan, B, nshift, S) bytes, 256-byte aligned
+ *   shift_out   device, B ints: index j of the best shift
+ *   quat_out    device, B * 4 floats; score_out device, B floats
+ *   opts        as bh_align_batch (tmpl_index, group, starts_per_thread); per-start outputs and FP64
+ *               re-scoring are not available here
+ * Uses the plan's expansion scratch (serialise calls on one plan).
+ */
+size_t bh_align_shifts_workspace(const bh_plan* plan, int B, int nshift, int S);
+int bh_align_shifts(bh_plan* plan, const float* tmpl, const float* vols, int B, const int* shifts, int nshift,
+                    const float* starts, int S, const int* stages, int nstages, int steps, void* workspace,
+                    size_t workspace_bytes, int* shift_out, float* quat_out, float* score_out,
+                    const bh_align_opts* opts, void* stream);
+
 /* ------------------------------------------------------------------ autotuning */
 typedef struct {
   int align_group;  /* lanes per start (per pair of starts when align_starts_per_thread = 2) chosen for

@@ -152,3 +152,23 @@ def rotate_coeffs(basis: Basis, coeffs: np.ndarray, q) -> np.ndarray:
         blk = out[o0:o1].reshape(-1, 2 * l + 1)
         out[o0:o1] = (blk @ D.T).ravel()
     return out
+
+
+@dataclass
+class ShiftResult:
+    shift: int  # index of the best shift
+    q: np.ndarray
+    score: float
+    per_shift: list
+
+
+def align_shifts(basis: Basis, t_hat, vol, shifts, starts: np.ndarray, stages: list[int], steps: int) -> ShiftResult:
+    """Eq. 1 over a grid of shifts (Sec. II-C): for each shift s, expand f_s(x) = f(x + s) and maximise Eq. 2
+    from the same starts; keep the (shift, rotation) with the largest final score (ties: lowest shift index)."""
+    from .ball import expand, shift_volume
+    res = []
+    for s in shifts:
+        f_hat = expand(basis, shift_volume(vol, s))[0]
+        res.append(align_particle(basis, t_hat, f_hat, starts, stages, steps))
+    best = select_best(np.array([r.score for r in res]))
+    return ShiftResult(best, res[best].q, res[best].score, res)

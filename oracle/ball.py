@@ -216,3 +216,17 @@ def split_by_degree(basis: Basis, coeffs: np.ndarray) -> list[np.ndarray]:
         o0, o1 = basis.offsets[l], basis.offsets[l + 1]
         out.append(np.asarray(coeffs[o0:o1]).reshape(len(basis.roots[l]), 2 * l + 1))
     return out
+
+
+def shift_volume(vol: np.ndarray, s) -> np.ndarray:
+    """f_s(x) = f(x + s) on the voxel grid for an integer shift s = (sx, sy, sz) voxels, zero where x + s
+    leaves the box (Eq. 1's shifted subtomogram; array order [z][y][x])."""
+    vol = np.asarray(vol)
+    N = vol.shape[0]
+    sx, sy, sz = (int(v) for v in s)
+    out = np.zeros_like(vol)
+    i = np.arange(N)
+    ox, oy, oz = i + sx, i + sy, i + sz
+    vx, vy, vz = (ox >= 0) & (ox < N), (oy >= 0) & (oy < N), (oz >= 0) & (oz < N)
+    out[np.ix_(vz, vy, vx)] = vol[np.ix_(oz[vz], oy[vy], ox[vx])]
+    return out

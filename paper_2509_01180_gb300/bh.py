@@ -22,7 +22,7 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
-           "bh_align_batch", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
@@ -226,6 +226,29 @@ def bh_random_starts(seed: int, B: int, S: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ serving
+def bh_align_shifts(plan: Plan, tmpl, vols, shifts, starts, stages, steps: int, group: int = 0,
+                    starts_per_thread: int = 0, stream=None):
+    """Shift grid x rotational matching: returns (best shift index (B,), quat (B,4), score (B,))."""
+    import torch
+    B, S = starts.shape[0], starts.shape[1]
+    sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.int32).reshape(-1, 3))
+    ns = sh.shape[0]
+    _need(vols, "torch.float32", B * plan.N ** 3, "vols")
+    _need(starts, "torch.float32", B * S * 4, "starts")
+    nbytes = int(lib().bh_align_shifts_workspace(plan.handle, B, ns, S))
+    ws = torch.empty((max(nbytes, 256) + 255) // 256 * 256 // 4, dtype=torch.float32, device=vols.device)
+    idx = torch.empty((B,), dtype=torch.int32, device=vols.device)
+    quat = torch.empty((B, 4), dtype=torch.float32, device=vols.device)
+    score = torch.empty((B,), dtype=torch.float32, device=vols.device)
+    st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
+    o = AlignOpts()
+    o.group, o.starts_per_thread = group, starts_per_thread
+    _check(lib().bh_align_shifts(plan.handle, _ptr(tmpl), _ptr(vols), B, sh.ctypes.data, ns, _ptr(starts), S, st,
+                                 len(stages), steps, _ptr(ws), ws.numel() * 4, _ptr(idx), _ptr(quat), _ptr(score),
+                                 ctypes.byref(o), _stream(stream)), "bh_align_shifts")
+    return idx, quat, score
+
+
 def bh_energy(plan: Plan, tmpl, sub, L: int, tmpl_index=None, n_templates: int = 0, stream=None):
     """Per-degree energy E_l (B, L+1) of xi^l and the energy ratio Ratio(L') = sum_{l>L'} E_l / sum E_l."""
     import torch
@@ -276,6 +299,10 @@ def _serve_sigs(L):
     L.bh_random_starts.argtypes = [ctypes.c_uint64, i, i, vp]
     L.bh_autotune.argtypes = [vp, i, i, vp, i, i, ctypes.POINTER(TuneResult)]
     L.bh_energy.argtypes = [vp, vp, vp, i, i, vp, i, vp, vp]
+    L.bh_align_shifts_workspace.argtypes = [vp, i, i, i]
+    L.bh_align_shifts_workspace.restype = ctypes.c_size_t
+    L.bh_align_shifts.argtypes = [vp, vp, vp, i, vp, i, vp, i, vp, i, i, vp, ctypes.c_size_t, vp, vp, vp,
+                                  ctypes.POINTER(AlignOpts), vp]
     L.bh_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServeOpts)]
     L.bh_serve_add_template.argtypes = [vp, i, vp, ctypes.POINTER(i)]
     L.bh_serve_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -284,7 +311,7 @@ def _serve_sigs(L):
     L.bh_serve_pause.argtypes = [vp, i]
     L.bh_serve_stats.argtypes = [vp, ctypes.POINTER(ServeCounters)]
     L.bh_serve_destroy.argtypes = [vp]
-    for n in ("bh_random_starts", "bh_autotune", "bh_energy", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
+    for n in ("bh_random_starts", "bh_autotune", "bh_energy", "bh_align_shifts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
               "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"):
         getattr(L, n).restype = i
     L._serve_ready = True

@@ -31,9 +31,12 @@
 //
 // Work split: one CTA per subtomogram; lane group of G threads per start; within a row m the 2m+1
 // orbits are dealt round-robin to the G lanes, which reduce their partial sums by xor-shuffles.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <memory>
 #include <mutex>
+#include <vector>
 
 #include "bh_internal.h"
 
@@ -723,15 +726,18 @@ int launch_refine_g(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStre
   return BH_OK;
 }
 
+// FP64 work needs many warps in flight; one CTA per subtomogram holds K re-scored starts with up to a full
+// warp of lanes each (at least 128 threads when K allows).
 int launch_refine(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
   int G = 1;
-  while (G < 16 && K * G < 128 && K * G * 2 <= kMaxThreads) G *= 2;
+  while (G < 32 && K * G < 256 && K * G * 2 <= kMaxThreads) G *= 2;
   switch (G) {
     case 1: return launch_refine_g<1>(a, L, K, p, stream);
     case 2: return launch_refine_g<2>(a, L, K, p, stream);
     case 4: return launch_refine_g<4>(a, L, K, p, stream);
     case 8: return launch_refine_g<8>(a, L, K, p, stream);
-    default: return launch_refine_g<16>(a, L, K, p, stream);
+    case 16: return launch_refine_g<16>(a, L, K, p, stream);
+    default: return launch_refine_g<32>(a, L, K, p, stream);
   }
 }
 
@@ -997,6 +1003,88 @@ extern "C" int bh_energy(const bh_plan* p, const float* tmpl, const float* sub, 
   k_energy<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(p->layout, reinterpret_cast<const float2*>(tmpl),
                                                                  tmpl_index, n_templates,
                                                                  reinterpret_cast<const float2*>(sub), L, energy);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+// ---------------------------------------------------------------------------- shift search
+namespace bh {
+namespace {
+__global__ void k_repeat_starts(const float4* __restrict__ starts, int B, int S, int nshift, float4* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t total = (size_t)B * nshift * S;
+  if (i >= total) return;
+  const size_t s = i % S, r = i / S, b = r / nshift;
+  out[i] = starts[b * S + s];
+}
+
+// Best shift per subtomogram by final score (exact ties: lowest shift index).
+__global__ void k_select_shift(const float4* __restrict__ quat, const float* __restrict__ score, int B, int nshift,
+                               int* __restrict__ shift_out, float4* __restrict__ quat_out, float* __restrict__ score_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  int best = 0;
+  for (int j = 1; j < nshift; ++j)
+    if (score[(size_t)b * nshift + j] > score[(size_t)b * nshift + best]) best = j;
+  shift_out[b] = best;
+  quat_out[b] = quat[(size_t)b * nshift + best];
+  score_out[b] = score[(size_t)b * nshift + best];
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+}  // namespace
+}  // namespace bh
+
+extern "C" size_t bh_align_shifts_workspace(const bh_plan* p, int B, int nshift, int S) {
+  if (!p || B < 0 || nshift < 1 || S < 1) return 0;
+  const size_t R = (size_t)B * nshift;
+  return align256((size_t)nshift * sizeof(int3)) + align256(R * p->Nb * 8) + align256(R * S * 16) + align256(R * 16) +
+         align256(R * 4);
+}
+
+extern "C" int bh_align_shifts(bh_plan* p, const float* tmpl, const float* vols, int B, const int* shifts, int nshift,
+                               const float* starts, int S, const int* stages, int nstages, int steps, void* workspace,
+                               size_t workspace_bytes, int* shift_out, float* quat_out, float* score_out,
+                               const bh_align_opts* opts, void* stream_) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 0 || nshift < 1 || nshift > 4096 || S < 1) return fail(BH_ERR_ARG, "B=%d nshift=%d S=%d", B, nshift, S);
+  if (B == 0) return BH_OK;
+  if (!tmpl || !vols || !shifts || !starts || !workspace || !shift_out || !quat_out || !score_out)
+    return fail(BH_ERR_ARG, "NULL argument");
+  if (opts && (opts->start_quat_out || opts->start_score_out || opts->refine_fp64))
+    return fail(BH_ERR_ARG, "per-start outputs and FP64 re-scoring are not available with shifts");
+  if ((long long)B * nshift > (1LL << 30)) return fail(BH_ERR_ARG, "B * nshift too large");
+  const size_t need = bh_align_shifts_workspace(p, B, nshift, S);
+  if (workspace_bytes < need) return fail(BH_ERR_ARG, "workspace of %zu bytes, %zu needed", workspace_bytes, need);
+  for (int j = 0; j < nshift; ++j)
+    for (int d = 0; d < 3; ++d)
+      if (shifts[3 * j + d] <= -p->N || shifts[3 * j + d] >= p->N)
+        return fail(BH_ERR_ARG, "shift %d component %d = %d outside the box", j, d, shifts[3 * j + d]);
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const size_t R = (size_t)B * nshift;
+  char* w = static_cast<char*>(workspace);
+  int3* d_shifts = reinterpret_cast<int3*>(w);
+  w += align256((size_t)nshift * sizeof(int3));
+  float* coeffs = reinterpret_cast<float*>(w);
+  w += align256(R * p->Nb * 8);
+  float4* rep = reinterpret_cast<float4*>(w);
+  w += align256(R * S * 16);
+  float4* q_all = reinterpret_cast<float4*>(w);
+  w += align256(R * 16);
+  float* s_all = reinterpret_cast<float*>(w);
+  BH_CUDA_TRY(cudaMemcpyAsync(d_shifts, shifts, (size_t)nshift * sizeof(int3), cudaMemcpyHostToDevice, stream));
+  int st = expand_shifted(p, vols, B, d_shifts, nshift, coeffs, stream);
+  if (st != BH_OK) return st;
+  const size_t n = R * S;
+  k_repeat_starts<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(reinterpret_cast<const float4*>(starts), B, S, nshift,
+                                                                  rep);
+  BH_CHECK_LAUNCH();
+  st = bh_align_batch(p, tmpl, coeffs, (int)R, reinterpret_cast<const float*>(rep), S, stages, nstages, steps,
+                      reinterpret_cast<float*>(q_all), s_all, opts, stream);
+  if (st != BH_OK) return st;
+  k_select_shift<<<(B + 127) / 128, 128, 0, stream>>>(q_all, s_all, B, nshift, shift_out,
+                                                      reinterpret_cast<float4*>(quat_out), score_out);
   BH_CHECK_LAUNCH();
   return BH_OK;
 }

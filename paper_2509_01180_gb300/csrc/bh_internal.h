@@ -91,6 +91,8 @@ int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const 
                  const std::vector<int>& vox_r2, const std::vector<int2>& colinfo, double h3);
 int make_tensor_maps(bh_plan* p);
 int set_gemm_bn(bh_plan* p, int bn);
+int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, int nshift, float* coeffs,
+                   cudaStream_t stream);
 int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scratch_x, float* scratch_c, int rows_cap,
                 cudaStream_t stream);
 // align.cu

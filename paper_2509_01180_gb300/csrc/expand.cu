@@ -56,6 +56,34 @@ __global__ void k_gather(const float* __restrict__ vols, int B, long long N3, co
   }
 }
 
+// ---------------------------------------------------------------- gather of shifted volumes
+// Row r = b * nshift + j holds the in-ball voxels of f_s(x) = f(x + s_j) for volume b (zero where x + s_j
+// leaves the box); shifts are integer voxels (sx, sy, sz).
+__global__ void k_gather_shifted(const float* __restrict__ vols, int B, int N, const int* __restrict__ vox,
+                                 const int3* __restrict__ shifts, int nshift, int row0, int rows, int V, int V_pad,
+                                 float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
+                                 __nv_bfloat16* __restrict__ Xlo) {
+  const int rr = blockIdx.y;  // row within this pass
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V_pad) return;
+  const int r = row0 + rr;
+  float x = 0.0f;
+  if (rr < rows && v < V) {
+    const int b = r / nshift, j = r % nshift;
+    const int idx = vox[v];
+    const int ix = idx % N + shifts[j].x, iy = (idx / N) % N + shifts[j].y, iz = idx / (N * N) + shifts[j].z;
+    if (b < B && ix >= 0 && ix < N && iy >= 0 && iy < N && iz >= 0 && iz < N)
+      x = __ldg(vols + (size_t)b * N * N * N + ((size_t)iz * N + iy) * N + ix);
+  }
+  const size_t o = (size_t)rr * V_pad + v;
+  if (X32) X32[o] = x;
+  if (Xhi) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+    Xhi[o] = hi;
+    Xlo[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
+  }
+}
+
 // ---------------------------------------------------------------- real columns -> complex coefficients
 // slot[s] = (re source, im source), 1-based column index with sign, 0 = zero.
 // With split-K the GEMM leaves `splits` partial products `split_stride` floats apart; they are summed
@@ -593,6 +621,35 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
     dim3 g2((p->Nb + 255) / 256, Bc);
     k_to_complex<<<g2, 256, 0, stream>>>(scratch_c, p->Nb_pad, Bc, p->Nb, p->d_slot,
                                          reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb, 1, 0);
+    BH_CHECK_LAUNCH();
+  }
+  return BH_OK;
+}
+
+// Expansion of every (volume, shift) pair into coeffs [b][shift][Nb], through the plan's scratch.
+int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, int nshift, float* coeffs,
+                   cudaStream_t stream) {
+  const int total = B * nshift;
+  for (int r0 = 0; r0 < total; r0 += p->max_batch) {
+    const int rows = std::min(p->max_batch, total - r0);
+    const int Mp = round_up(rows, kGemmBM);
+    dim3 g1((p->V_pad + 255) / 256, Mp);
+    k_gather_shifted<<<g1, 256, 0, stream>>>(vols, B, p->N, p->d_vox, d_shifts, nshift, r0, rows, p->V, p->V_pad,
+                                             p->d_X32, p->d_Xhi, p->d_Xlo);
+    BH_CHECK_LAUNCH();
+    const int splits = choose_splits(p, Mp);
+    int st = launch_gemm(p, Mp, splits, stream);
+    if (st != BH_OK) return st;
+    const int nkb = p->V_pad / kGemmBK;
+    const int used = (p->mode == BH_MODE_FP32)
+                         ? (p->V_pad + round_up((p->V_pad + splits - 1) / splits, SG_BK) - 1) /
+                               round_up((p->V_pad + splits - 1) / splits, SG_BK)
+                         : (nkb + round_up((nkb + splits - 1) / splits, KCHUNK) - 1) /
+                               round_up((nkb + splits - 1) / splits, KCHUNK);
+    dim3 g2((p->Nb + 255) / 256, rows);
+    k_to_complex<<<g2, 256, 0, stream>>>(p->d_C, p->Nb_pad, rows, p->Nb, p->d_slot,
+                                         reinterpret_cast<float2*>(coeffs) + (size_t)r0 * p->Nb, used,
+                                         (size_t)p->M_cap * p->Nb_pad);
     BH_CHECK_LAUNCH();
   }
   return BH_OK;

@@ -80,9 +80,12 @@ def blob_template(rng: np.random.Generator, n_blobs: int, sigma: float, r_max: f
     return BlobTemplate(d * r[:, None], 0.5 + 0.5 * rng.random(n_blobs), float(sigma))
 
 
-def render(N: int, tpl: BlobTemplate, q=None) -> np.ndarray:
-    """Volume vol[z, y, x] of the blobs (rotated by q when given), centre at voxel N/2 along each axis."""
+def render(N: int, tpl: BlobTemplate, q=None, offset=None) -> np.ndarray:
+    """Volume vol[z, y, x] of the blobs (rotated by q, then displaced by `offset` voxels (x, y, z), when
+    given), centre at voxel N/2 along each axis."""
     c = tpl.centres if q is None else tpl.centres @ _rotation_matrix(q).T
+    if offset is not None:
+        c = c + np.asarray(offset, dtype=np.float64)[None, :]
     p = np.arange(N, dtype=np.float64) - N / 2
     s2 = 2.0 * tpl.sigma ** 2
     ex = np.exp(-(p[None, :] - c[:, 0:1]) ** 2 / s2) * tpl.amps[:, None]
@@ -249,3 +252,4 @@ def make_mixed(scale: float = 1.0, distinct: int | None = None, master: int = MA
         out.append(ClassWorkload(N, L, math.pi * N / 2, stages, 30, templates, vols[order], tidx[order],
                                  q_true[order], S[order], starts[order]))
     return out
+

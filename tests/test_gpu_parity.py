@@ -342,3 +342,27 @@ def test_energy_ratio_matches_oracle(dev):
         ref_e = np.array([np.sum(np.abs(x) ** 2) for x in xi])
         assert np.allclose(e[b], ref_e, rtol=1e-4, atol=1e-12 * ref_e.max())
         assert np.allclose(ratio[b], align.energy_ratio(xi), atol=1e-5)
+
+
+def test_shift_search_matches_oracle(dev):
+    """bh_align_shifts: expansion of every shifted copy, marching ascent, selection over shifts."""
+    w = synth.make_workload("pair16")
+    tpl = synth.blob_template(synth.rng_for(1, 0), 20, 1.2, 6.0)
+    s_true = (1, 0, -1)
+    vols = np.stack([synth.render(16, tpl, w.q_true[0], offset=s_true),
+                     synth.render(16, tpl, w.q_true[0], offset=(0, 0, 0))]).astype(np.float32)
+    starts = np.concatenate([w.starts, w.starts]).astype(np.float32)
+    shifts = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 0, -1), (1, 0, -1), (-1, 0, 1)]
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    tv = synth.render(16, tpl).astype(np.float32)
+    t_gpu = bh.bh_expand(p, torch.from_numpy(tv[None]).to(dev))[0].contiguous()
+    idx, q, sc = bh.bh_align_shifts(p, t_gpu, torch.from_numpy(vols).to(dev), shifts, torch.from_numpy(starts).to(dev),
+                                    [2, 4, 8], 30)
+    idx, q = idx.cpu().numpy(), q.cpu().numpy().astype(np.float64)
+    assert shifts[idx[0]] == s_true and shifts[idx[1]] == (0, 0, 0)
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, tv.astype(np.float64))[0]
+    for b in range(2):
+        ref = align.align_shifts(Bs, t, vols[b].astype(np.float64), shifts, starts[b].astype(np.float64), [2, 4, 8], 30)
+        assert ref.shift == idx[b]
+        assert math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), ref.q)) < 0.1

@@ -130,3 +130,18 @@ def test_marching_on_noiseless_voxel_phantom():
     res = align.align_particle(Bs, t, f, w.starts[0].astype(np.float64), w.stages, w.steps)
     err = math.degrees(wigner.geodesic_angle(res.q, quat_conj(w.q_true[0])))
     assert err < 3.0, err
+
+
+def test_shift_search_recovers_shift_and_rotation():
+    """Eq. 1 over a shift grid: a noiseless phantom rotated by R and displaced by s_true is matched at
+    s_true (f_s(x) = f(x + s) undoes the displacement) with R close to R_true^{-1}."""
+    w = synth.make_workload("pair16")
+    tpl = synth.blob_template(synth.rng_for(1, 0), 20, 1.2, 6.0)
+    s_true = (1, 0, -1)
+    vol = synth.render(16, tpl, w.q_true[0], offset=s_true)
+    Bs = ball.make_basis(8, 8 * math.pi)
+    t = ball.expand(Bs, synth.render(16, tpl))[0]
+    shifts = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 0, -1), (1, 0, -1), (-1, 0, 1)]
+    res = align.align_shifts(Bs, t, vol, shifts, w.starts[0].astype(np.float64), [2, 4, 8], 30)
+    assert shifts[res.shift] == s_true
+    assert math.degrees(wigner.geodesic_angle(res.q, quat_conj(w.q_true[0]))) < 3.0

@@ -251,3 +251,17 @@ def test_voxel_expansion_converges_to_projection():
         errs.append(np.linalg.norm(a - coef) / np.linalg.norm(coef))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.05
+
+
+def test_shift_volume_definition():
+    rng = np.random.default_rng(8)
+    v = rng.normal(size=(8, 8, 8))
+    s = (2, -1, 3)
+    out = ball.shift_volume(v, s)
+    for z, y, x in ((0, 1, 0), (4, 4, 4), (2, 7, 5)):
+        zz, yy, xx = z + s[2], y + s[1], x + s[0]
+        ref = v[zz, yy, xx] if (0 <= zz < 8 and 0 <= yy < 8 and 0 <= xx < 8) else 0.0
+        assert out[z, y, x] == ref
+    # shifting back restores the overlap
+    back = ball.shift_volume(out, (-2, 1, -3))
+    assert np.array_equal(back[3:8, 0:7, 2:8], v[3:8, 0:7, 2:8])
