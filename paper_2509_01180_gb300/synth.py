@@ -253,3 +253,19 @@ def make_mixed(scale: float = 1.0, distinct: int | None = None, master: int = MA
                                  q_true[order], S[order], starts[order]))
     return out
 
+
+# ---------------------------------------------------------------------------------- rotation grids
+def super_fibonacci(n: int) -> np.ndarray:
+    """n quasi-uniform rotations (w, x, y, z) from super-Fibonacci spirals (M. Alexa, "Super-Fibonacci
+    Spirals: Fast, Low-Discrepancy Sampling of SO(3)", CVPR 2022): s_i = i + 1/2, r = sqrt(s/n),
+    R = sqrt(1 - s/n), alpha = 2 pi s / phi, beta = 2 pi s / psi with phi = sqrt(2) and psi the real root
+    of psi^4 = psi + 4; q_i = (r sin alpha, r cos alpha, R sin beta, R cos beta).  Returned as float32 with
+    w >= 0 (q and -q are the same rotation)."""
+    phi = math.sqrt(2.0)
+    psi = 1.533751168755204288118041
+    s = np.arange(n, dtype=np.float64) + 0.5
+    r, R = np.sqrt(s / n), np.sqrt(1.0 - s / n)
+    a, b = 2 * math.pi * s / phi, 2 * math.pi * s / psi
+    q = np.stack([r * np.sin(a), r * np.cos(a), R * np.sin(b), R * np.cos(b)], axis=1)
+    q *= np.where(q[:, :1] < 0, -1.0, 1.0)
+    return q.astype(np.float32)
