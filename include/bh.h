@@ -228,6 +228,45 @@ int bh_align_shifts(bh_plan* plan, const float* tmpl, const float* vols, int B, 
                     size_t workspace_bytes, int* shift_out, float* quat_out, float* score_out,
                     const bh_align_opts* opts, void* stream);
 
+/* ------------------------------------------------------------------ candidate starts */
+/*
+ * Rotation grid for candidate starts (Sec. III: the initial candidates are the local maxima of Eq. 2
+ * truncated at the lowest selected band).  The grid is uploaded to the current device and its
+ * neighbour lists are built there: j != i is a neighbour of i when |q_i . q_j| >= cos(radius / 2)
+ * (geodesic angle <= radius), the dot product summed in the order w, x, y, z in FP64.
+ *   quats   host, n * 4 floats (w, x, y, z), unit quaternions; n in 1..16384; copied
+ *   radius  neighbourhood radius in radians, [0, pi]
+ * The grid is owned by the caller and freed by bh_grid_destroy.  Synchronous.
+ */
+typedef struct bh_grid bh_grid;
+int bh_grid_create(bh_grid** out, const float* quats, int n, double radius);
+int bh_grid_destroy(bh_grid* grid);
+/* Grid size, largest neighbour count and total neighbour entries (any output may be NULL). */
+int bh_grid_info(const bh_grid* grid, int* n, int* max_neighbors, long long* n_edges);
+/* Copy the neighbour lists to the host in CSR form: offsets (n+1 ints), neighbors (cap >= n_edges ints,
+   ascending within each list).  Synchronous. */
+int bh_grid_neighbors(const bh_grid* grid, int* offsets, int* neighbors, long long cap);
+
+/*
+ * Candidate starts for B subtomograms, one launch.  For each subtomogram: Eq. 2 truncated at band L
+ * at every grid rotation (FP32, the alignment's evaluation); grid point i ranks above j when its
+ * score is larger, or equal with i < j; i is a local maximum when it ranks above all of its
+ * neighbours.  The candidates are the local maxima in rank order followed, if there are fewer than
+ * S, by the other grid points in rank order; the first S are written.
+ *   L               band, 1..Lmax (the lowest marching band; the grid scores' orbit table of band L and
+ *                   the sort keys share one CTA's shared memory: 16-byte table entries plus 8 bytes
+ *                   per grid point rounded up to a power of two, at most 227 KB)
+ *   tmpl, sub, tmpl_index, n_templates   as bh_align_batch
+ *   S               1..n candidates per subtomogram
+ *   starts_out      device, B * S * 4 floats: the candidate rotations (grid entries as given), ready
+ *                   as `starts` of bh_align_batch
+ *   index_out       device, B * S ints (grid indices) or NULL
+ *   grid_score_out  device, B * n floats (band-L score of every grid rotation) or NULL
+ */
+int bh_candidates(const bh_plan* plan, const bh_grid* grid, const float* tmpl, const float* sub, int B, int L,
+                  const int* tmpl_index, int n_templates, int S, float* starts_out, int* index_out,
+                  float* grid_score_out, void* stream);
+
 /* ------------------------------------------------------------------ autotuning */
 typedef struct {
   int align_group;  /* lanes per start (per pair of starts when align_starts_per_thread = 2) chosen for

@@ -22,7 +22,8 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
-           "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_grid_create", "bh_grid_destroy", "bh_grid_info",
+           "bh_grid_neighbors", "bh_candidates", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
@@ -67,6 +68,11 @@ def lib() -> ctypes.CDLL:
         L.bh_expand_noalloc.argtypes = [vp, vp, i, vp, vp]
         L.bh_score_grad.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp]
         L.bh_align_batch.argtypes = [vp, vp, vp, i, vp, i, vp, i, i, vp, vp, ctypes.POINTER(AlignOpts), vp]
+        L.bh_grid_create.argtypes = [ctypes.POINTER(vp), vp, i, d]
+        L.bh_grid_destroy.argtypes = [vp]
+        L.bh_grid_info.argtypes = [vp, vp, vp, vp]
+        L.bh_grid_neighbors.argtypes = [vp, vp, vp, ctypes.c_longlong]
+        L.bh_candidates.argtypes = [vp, vp, vp, vp, i, i, vp, i, i, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("bh_last_error", "bh_status_string"):
                 getattr(L, name).restype = i
@@ -247,6 +253,62 @@ def bh_align_shifts(plan: Plan, tmpl, vols, shifts, starts, stages, steps: int, 
                                  len(stages), steps, _ptr(ws), ws.numel() * 4, _ptr(idx), _ptr(quat), _ptr(score),
                                  ctypes.byref(o), _stream(stream)), "bh_align_shifts")
     return idx, quat, score
+
+
+# ------------------------------------------------------------------ candidate starts
+class Grid:
+    """Owning handle of a rotation grid with its neighbour lists on the device."""
+
+    def __init__(self, handle: int, radius: float):
+        self.handle = handle
+        self.radius = radius
+        n, mx, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _check(lib().bh_grid_info(handle, ctypes.byref(n), ctypes.byref(mx), ctypes.byref(ne)), "bh_grid_info")
+        self.n, self.max_neighbors, self.n_edges = n.value, mx.value, ne.value
+
+    def neighbors(self) -> list[np.ndarray]:
+        off = np.empty(self.n + 1, dtype=np.int32)
+        nb = np.empty(max(1, self.n_edges), dtype=np.int32)
+        _check(lib().bh_grid_neighbors(self.handle, off.ctypes.data, nb.ctypes.data, nb.size), "bh_grid_neighbors")
+        return [nb[off[i]:off[i + 1]].copy() for i in range(self.n)]
+
+    def destroy(self):
+        if self.handle:
+            lib().bh_grid_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def bh_grid_create(quats: np.ndarray, radius: float) -> Grid:
+    """Upload an (n, 4) rotation grid (w, x, y, z) and build its neighbour lists (geodesic angle <= radius)."""
+    q = np.ascontiguousarray(quats, dtype=np.float32).reshape(-1, 4)
+    h = ctypes.c_void_p()
+    _check(lib().bh_grid_create(ctypes.byref(h), q.ctypes.data, q.shape[0], float(radius)), "bh_grid_create")
+    return Grid(h.value, float(radius))
+
+
+def bh_candidates(plan: Plan, grid: Grid, tmpl, sub, L: int, S: int, tmpl_index=None, n_templates: int = 0,
+                  starts_out=None, with_index: bool = False, with_scores: bool = False, stream=None):
+    """Candidate starts from local maxima of the band-L score on the grid.  Returns (starts (B,S,4),
+    index (B,S) or None, grid scores (B,n) or None)."""
+    import torch
+    B = sub.shape[0]
+    dev = sub.device
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    _need(tmpl, "torch.float32", plan.Nb * 2 * max(1, n_templates), "tmpl")
+    starts = starts_out if starts_out is not None else torch.empty((B, S, 4), dtype=torch.float32, device=dev)
+    idx = torch.empty((B, S), dtype=torch.int32, device=dev) if with_index else None
+    sc = torch.empty((B, grid.n), dtype=torch.float32, device=dev) if with_scores else None
+    if tmpl_index is not None:
+        _need(tmpl_index, "torch.int32", B, "tmpl_index")
+    _check(lib().bh_candidates(plan.handle, grid.handle, _ptr(tmpl), _ptr(sub), B, L, _ptr(tmpl_index), n_templates,
+                               S, _ptr(starts), _ptr(idx), _ptr(sc), _stream(stream)), "bh_candidates")
+    return starts, idx, sc
 
 
 def bh_energy(plan: Plan, tmpl, sub, L: int, tmpl_index=None, n_templates: int = 0, stream=None):

@@ -1088,3 +1088,245 @@ extern "C" int bh_align_shifts(bh_plan* p, const float* tmpl, const float* vols,
   BH_CHECK_LAUNCH();
   return BH_OK;
 }
+
+// ---------------------------------------------------------------------------- candidate starts (Sec. III)
+struct bh_grid {
+  int device = 0;
+  int n = 0;
+  int npow2 = 0;
+  int max_nbr = 0;
+  long long n_edges = 0;
+  double radius = 0.0;
+  float4* d_q = nullptr;   // [n] rotations (w, x, y, z) as given
+  int* d_off = nullptr;    // [n + 1] CSR offsets of the neighbour lists
+  int* d_nbr = nullptr;    // [n_edges] neighbour indices, ascending per grid point
+};
+
+namespace bh {
+namespace {
+constexpr int kGridMax = 16384;  // the sort keys of one subtomogram's grid scores live in shared memory
+constexpr int kCandThreads = 256;
+
+// |q_i . q_j| >= c, the dot product summed in the order w, x, y, z in FP64 (exact products of floats).
+__device__ __forceinline__ bool within(float4 a, float4 b, double c) {
+  double d = __dmul_rn((double)a.x, (double)b.x);
+  d = __dadd_rn(d, __dmul_rn((double)a.y, (double)b.y));
+  d = __dadd_rn(d, __dmul_rn((double)a.z, (double)b.z));
+  d = __dadd_rn(d, __dmul_rn((double)a.w, (double)b.w));
+  return fabs(d) >= c;
+}
+
+// Pass 1 (count) and pass 2 (fill, off != NULL) of the neighbour lists; one thread per grid point.
+__global__ void k_grid_nbr(const float4* __restrict__ q, int n, double c, const int* __restrict__ off,
+                           int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 qi = q[i];
+  int cnt = 0;
+  int* dst = off ? out + off[i] : nullptr;
+  for (int j = 0; j < n; ++j) {
+    if (j == i || !within(qi, q[j], c)) continue;
+    if (dst) dst[cnt] = j;
+    ++cnt;
+  }
+  if (!off) out[i] = cnt;
+}
+
+// Sort key of grid point i: [local-maximum flag : 1][score, order-preserving bits : 32][~i : 31], so that a
+// larger key ranks higher (larger score; equal scores: lower index) and local maxima come first.
+__device__ __forceinline__ unsigned long long grid_key(float s, int i) {
+  unsigned u = __float_as_uint(s);
+  u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  return ((unsigned long long)u << 31) | (unsigned long long)(0x7FFFFFFF - i);
+}
+
+struct GridArgs {
+  const float4* q;
+  int n, npow2;
+  const int* off;
+  const int* nbr;
+  int L;
+  float4* starts_out;  // [B][S]
+  int* index_out;      // [B][S] or NULL
+  float* score_out;    // [B][n] or NULL
+};
+
+// One CTA per subtomogram: Eq. 2 at band L on every grid rotation (orbit table of band L in shared memory),
+// local-maximum flags from the neighbour lists, a bitonic sort of the keys, the first S grid rotations out.
+template <int C>
+__global__ void __launch_bounds__(kCandThreads, 2) k_grid_candidates(const AlignArgs a, const GridArgs g) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  const int ntab = tab_base(a.Lb + 1, a.Lb);
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_tab + ntab);
+  unsigned* flag = reinterpret_cast<unsigned*>(key + g.npow2);
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
+  for (int w = threadIdx.x; w < (g.npow2 >> 5); w += blockDim.x) flag[w] = 0u;
+  for (int i = g.n + threadIdx.x; i < g.npow2; i += blockDim.x) key[i] = 0ull;  // padding ranks last
+  __syncthreads();
+  // every thread runs the same number of passes (the evaluation shuffles within warps)
+  const int per_pass = blockDim.x * C;
+  const int passes = (g.n + per_pass - 1) / per_pass;
+  for (int it = 0; it < passes; ++it) {
+    float4 q[C];
+    int idx[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      idx[j] = it * per_pass + j * blockDim.x + threadIdx.x;
+      q[j] = qnormalize(g.q[idx[j] < g.n ? idx[j] : g.n - 1]);
+    }
+    Eval e[C];
+    eval_rotations<1, C>(smem_tab, a.Lb, g.L, q, 0, a.lbin, e);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      if (idx[j] < g.n) {
+        key[idx[j]] = grid_key(e[j].S, idx[j]);
+        if (g.score_out) g.score_out[(size_t)p * g.n + idx[j]] = e[j].S;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+    const unsigned long long ki = key[i];
+    bool mx = true;
+    for (int e = g.off[i], e1 = g.off[i + 1]; e < e1 && mx; ++e) mx = key[g.nbr[e]] < ki;
+    if (mx) atomicOr(flag + (i >> 5), 1u << (i & 31));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x)
+    if ((flag[i >> 5] >> (i & 31)) & 1u) key[i] |= 1ull << 63;
+  __syncthreads();
+  // bitonic sort, descending
+  for (int k = 2; k <= g.npow2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (g.npow2 >> 1); t += blockDim.x) {
+        const int i = 2 * t - (t & (j - 1)), l = i + j;
+        const unsigned long long x = key[i], y = key[l];
+        if ((x < y) == ((i & k) == 0)) {
+          key[i] = y;
+          key[l] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int s = threadIdx.x; s < a.S; s += blockDim.x) {
+    const int i = 0x7FFFFFFF - (int)(key[s] & 0x7FFFFFFFull);
+    g.starts_out[(size_t)p * a.S + s] = g.q[i];
+    if (g.index_out) g.index_out[(size_t)p * a.S + s] = i;
+  }
+}
+
+size_t grid_smem(int L, int npow2) {
+  return table_bytes(L) + (size_t)npow2 * 8 + (size_t)(npow2 / 32) * 4;
+}
+}  // namespace
+}  // namespace bh
+
+extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double radius) {
+  clear_error();
+  if (!out) return fail(BH_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!quats) return fail(BH_ERR_ARG, "quats is NULL");
+  if (n < 1 || n > kGridMax) return fail(BH_ERR_ARG, "n=%d outside 1..%d", n, kGridMax);
+  if (!(radius >= 0.0 && radius <= 3.141592653589793)) return fail(BH_ERR_ARG, "radius=%g outside [0, pi]", radius);
+  for (int i = 0; i < 4 * n; ++i)
+    if (!std::isfinite(quats[i])) return fail(BH_ERR_ARG, "grid rotation %d is not finite", i / 4);
+  std::unique_ptr<bh_grid, int (*)(bh_grid*)> g(new bh_grid(), bh_grid_destroy);
+  BH_CUDA_TRY(cudaGetDevice(&g->device));
+  g->n = n;
+  g->radius = radius;
+  g->npow2 = 32;
+  while (g->npow2 < n) g->npow2 <<= 1;
+  const double c = std::cos(radius / 2);
+  BH_CUDA_TRY(cudaMalloc(&g->d_q, (size_t)n * sizeof(float4)));
+  BH_CUDA_TRY(cudaMalloc(&g->d_off, (size_t)(n + 1) * sizeof(int)));
+  BH_CUDA_TRY(cudaMemcpy(g->d_q, quats, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice));
+  int* d_cnt = nullptr;
+  BH_CUDA_TRY(cudaMalloc(&d_cnt, (size_t)n * sizeof(int)));
+  k_grid_nbr<<<(n + 127) / 128, 128>>>(g->d_q, n, c, nullptr, d_cnt);
+  std::vector<int> cnt(n), off(n + 1, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), d_cnt, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d_cnt);
+  if (e != cudaSuccess) return fail(BH_ERR_CUDA, "neighbour count: %s", cudaGetErrorString(e));
+  for (int i = 0; i < n; ++i) {
+    off[i + 1] = off[i] + cnt[i];
+    g->max_nbr = std::max(g->max_nbr, cnt[i]);
+  }
+  g->n_edges = off[n];
+  BH_CUDA_TRY(cudaMemcpy(g->d_off, off.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  BH_CUDA_TRY(cudaMalloc(&g->d_nbr, (size_t)std::max<long long>(1, g->n_edges) * sizeof(int)));
+  k_grid_nbr<<<(n + 127) / 128, 128>>>(g->d_q, n, c, g->d_off, g->d_nbr);
+  BH_CHECK_LAUNCH();
+  BH_CUDA_TRY(cudaDeviceSynchronize());
+  *out = g.release();
+  return BH_OK;
+}
+
+extern "C" int bh_grid_destroy(bh_grid* g) {
+  if (!g) return BH_OK;
+  cudaFree(g->d_q);
+  cudaFree(g->d_off);
+  cudaFree(g->d_nbr);
+  delete g;
+  return BH_OK;
+}
+
+extern "C" int bh_grid_info(const bh_grid* g, int* n, int* max_neighbors, long long* n_edges) {
+  clear_error();
+  if (!g) return fail(BH_ERR_ARG, "grid is NULL");
+  if (n) *n = g->n;
+  if (max_neighbors) *max_neighbors = g->max_nbr;
+  if (n_edges) *n_edges = g->n_edges;
+  return BH_OK;
+}
+
+extern "C" int bh_grid_neighbors(const bh_grid* g, int* offsets, int* neighbors, long long cap) {
+  clear_error();
+  if (!g) return fail(BH_ERR_ARG, "grid is NULL");
+  if (!offsets || (!neighbors && g->n_edges > 0)) return fail(BH_ERR_ARG, "NULL output");
+  if (cap < g->n_edges) return fail(BH_ERR_ARG, "cap %lld < %lld neighbour entries", cap, g->n_edges);
+  BH_CUDA_TRY(cudaMemcpy(offsets, g->d_off, (size_t)(g->n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  if (g->n_edges > 0)
+    BH_CUDA_TRY(cudaMemcpy(neighbors, g->d_nbr, (size_t)g->n_edges * sizeof(int), cudaMemcpyDeviceToHost));
+  return BH_OK;
+}
+
+extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float* tmpl, const float* sub, int B, int L,
+                             const int* tmpl_index, int n_templates, int S, float* starts_out, int* index_out,
+                             float* grid_score_out, void* stream) {
+  clear_error();
+  if (!p || !grid) return fail(BH_ERR_ARG, "plan or grid is NULL");
+  if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
+  if (L < 1 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 1..%d", L, p->Lmax);
+  if (S < 1 || S > grid->n) return fail(BH_ERR_ARG, "S=%d outside 1..%d (grid size)", S, grid->n);
+  if (tmpl_index && n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d with tmpl_index", n_templates);
+  if (B == 0) return BH_OK;
+  if (!tmpl || !sub || !starts_out) return fail(BH_ERR_ARG, "NULL array");
+  int dev = 0;
+  BH_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != grid->device) return fail(BH_ERR_ARG, "grid lives on device %d, current device is %d", grid->device, dev);
+  const size_t smem = grid_smem(L, grid->npow2);
+  if (smem > 232448) return fail(BH_ERR_ARG, "band %d with %d grid points needs %zu bytes of shared memory", L, grid->n, smem);
+  AlignArgs a{};
+  a.lay = p->layout;
+  a.tmpl = reinterpret_cast<const float2*>(tmpl);
+  a.tmpl_index = tmpl_index;
+  a.n_templates = n_templates;
+  a.sub = reinterpret_cast<const float2*>(sub);
+  a.B = B;
+  a.S = S;
+  a.Lb = L;
+  a.P = p->d_P;
+  a.lbin = p->d_lbin;
+  GridArgs g{grid->d_q, grid->n, grid->npow2, grid->d_off, grid->d_nbr, L,
+             reinterpret_cast<float4*>(starts_out), index_out, grid_score_out};
+  static std::atomic<int> have{0};
+  int st = ensure_smem(k_grid_candidates<2>, have, smem);
+  if (st != BH_OK) return st;
+  k_grid_candidates<2><<<B, kCandThreads, smem, static_cast<cudaStream_t>(stream)>>>(a, g);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
