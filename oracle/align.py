@@ -25,6 +25,12 @@ Readings where the paper is silent, garbled or ambiguous:
   * Selection: argmax over starts of the final-stage score; ties within 1e-12 |S|
     go to the lowest start index.
   * Energy ratio: the Fig. 1 caption omits the sums over m, m'; the reading sums them.
+  * Newton steps (Sec. III names them, without details): the Hessian is the second derivative of
+    S(R exp(eps.J)) at eps = 0, H_ij = -Re sum xi^l_{mm'} [D^l(R) (J_i J_j + J_j J_i) / 2]_{mm'}.
+    Per stage with band L, T iterations: stop if |g| <= 1e-12 |S|; if H is negative definite the
+    direction is d = -H^{-1} g, else the gradient step d = (pi/(2L)) g/|g|; d is clipped to length
+    pi/L and scaled by a damping factor lam (1 at the stage start); the trial R exp(d.J) is accepted if
+    it raises S (then lam <- min(1, 2 lam)), else lam <- lam/2.
 """
 from __future__ import annotations
 
@@ -61,6 +67,22 @@ def score_grad(xi: list[np.ndarray], q, L: int) -> tuple[float, np.ndarray]:
         for i in range(3):
             g[i] += float(np.real(np.sum(xi[l] * (D @ (-1j * J[i])))))
     return S, g
+
+
+def score_grad_hess(xi: list[np.ndarray], q, L: int) -> tuple[float, np.ndarray, np.ndarray]:
+    """Eq. 2, its body-frame gradient and Hessian along R(q) exp(eps.J) (Newton steps, Sec. III)."""
+    S = 0.0
+    g = np.zeros(3)
+    H = np.zeros((3, 3))
+    for l in range(L + 1):
+        D = wigner_D(l, q)
+        J = _j(l)
+        S += float(np.real(np.sum(xi[l] * D)))
+        for i in range(3):
+            g[i] += float(np.real(np.sum(xi[l] * (D @ (-1j * J[i])))))
+            for k in range(3):
+                H[i, k] -= 0.5 * float(np.real(np.sum(xi[l] * (D @ (J[i] @ J[k] + J[k] @ J[i])))))
+    return S, g, H
 
 
 def _normalize(q):
@@ -107,6 +129,46 @@ def ascend(xi: list[np.ndarray], q0, stages: list[int], steps: int) -> StartResu
     return StartResult(q, S, accepted, evals)
 
 
+def newton(xi: list[np.ndarray], q0, stages: list[int], steps: int) -> StartResult:
+    """Damped Newton iteration of one start with frequency marching (Sec. III, Sec. II-C)."""
+    q = _normalize(q0)
+    S = 0.0
+    accepted = 0
+    evals = 0
+    for L in stages:
+        if L < 1:
+            raise ValueError("marching bands must be >= 1")
+        h0, hmax = math.pi / (2 * L), math.pi / L
+        S, g, H = score_grad_hess(xi, q, L)
+        evals += 1
+        lam = 1.0
+        for _ in range(steps):
+            gn = float(np.linalg.norm(g))
+            if gn <= 1e-12 * abs(S):
+                break
+            if np.linalg.eigvalsh(H).max() < 0:
+                d = -np.linalg.solve(H, g)
+            else:
+                d = h0 * g / gn
+            dn = float(np.linalg.norm(d))
+            if dn > hmax:
+                d = d * (hmax / dn)
+                dn = hmax
+            d = lam * d
+            dn = lam * dn
+            step = np.array([math.cos(dn / 2), *(math.sin(dn / 2) * d / dn)]) if dn > 0 else np.array([1.0, 0, 0, 0])
+            qt = _normalize(quat_mul(q, step))
+            St, gt, Ht = score_grad_hess(xi, qt, L)
+            evals += 1
+            if St > S:
+                q, S, g, H = qt, St, gt, Ht
+                lam = min(1.0, 2 * lam)
+                accepted += 1
+            else:
+                lam = lam / 2
+    return StartResult(q, S, accepted, evals)
+
+
 def select_best(scores: np.ndarray) -> int:
     """Index of the largest final score; ties within 1e-12 |S| go to the lowest index."""
     best = 0
@@ -125,10 +187,12 @@ class AlignResult:
     best: int
 
 
-def align_particle(basis: Basis, t_hat, f_hat, starts: np.ndarray, stages: list[int], steps: int) -> AlignResult:
-    """One template/subtomogram pair: xi, every start's marching ascent, selection."""
+def align_particle(basis: Basis, t_hat, f_hat, starts: np.ndarray, stages: list[int], steps: int,
+                   method: str = "ascent") -> AlignResult:
+    """One template/subtomogram pair: xi, every start's marching ascent (or Newton iteration), selection."""
     xi = build_xi(basis, t_hat, f_hat, max(stages))
-    res = [ascend(xi, q0, stages, steps) for q0 in starts]
+    run = {"ascent": ascend, "newton": newton}[method]
+    res = [run(xi, q0, stages, steps) for q0 in starts]
     sc = np.array([r.score for r in res])
     qs = np.array([r.q for r in res])
     b = select_best(sc)

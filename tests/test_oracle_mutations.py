@@ -73,3 +73,25 @@ def test_xi_pin_catches_swapped_conjugation(monkeypatch):
 
     monkeypatch.setattr(align, "build_xi", bad)
     assert _fails(ta.test_score_is_eq1_inner_product_of_rotated_volume)
+
+
+@pytest.mark.parametrize("mutant", ["one_sided", "sign", "no_half"])
+def test_hessian_pin_catches_mistakes(monkeypatch, mutant):
+    def bad(xi, q, L):
+        S, g = align.score_grad(xi, q, L)
+        H = np.zeros((3, 3))
+        for l in range(L + 1):
+            D = wigner.wigner_D(l, q)
+            J = wigner._j(l)
+            for i in range(3):
+                for k in range(3):
+                    sym = J[i] @ J[k] + J[k] @ J[i]
+                    prod = {"one_sided": J[i] @ J[k], "sign": -sym / 2, "no_half": sym}[mutant]
+                    H[i, k] -= float(np.real(np.sum(xi[l] * (D @ prod))))
+        return S, g, H
+
+    monkeypatch.setattr(align, "score_grad_hess", bad)
+    Bs = ball.make_basis(4, 5 * math.pi)
+    rng = np.random.default_rng(2)
+    small = (Bs, rng.normal(size=Bs.Nb) + 1j * rng.normal(size=Bs.Nb), rng.normal(size=Bs.Nb) + 1j * rng.normal(size=Bs.Nb))
+    assert _fails(ta.test_hessian_matches_mixed_differences, small)
