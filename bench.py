@@ -318,12 +318,71 @@ def run_ours(args, rank, world, device):
                 e2e_ms += e0.elapsed_time(e1)
             flush.zero_()
         e2e_ms = replicas.max_over_ranks([e2e_ms], device)[0]
-        results[name] = {"plan_s": plan_s, "tune": tune, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
+        sec3 = sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) if (
+            name == "bf16split" and args.sec3) else None
+        results[name] = {"sec3": sec3, "plan_s": plan_s, "tune": tune, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
                          "clocks": clk.summary(), "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V,
                          "h2d": int(hv.numel() * 4), "d2h": int(hq.numel() * 4 + hs.numel() * 4)}
         plan.destroy()
         del coeffs
     return w, results
+
+
+def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
+    """The paper's own protocol (Sec. III) on the same batch: expansion, candidate starts from the local maxima
+    of the lowest marching band on a super-Fibonacci rotation grid, then damped Newton steps through the
+    marching bands.  Timed with CUDA events like the main leg (L2 flushed between steps)."""
+    import numpy as np
+    import torch
+
+    from paper_2509_01180_gb300 import bh, replicas, synth
+    B = w.B
+    n_grid, radius = args.sec3_grid, math.radians(args.sec3_radius)
+    grid = bh.bh_grid_create(synth.super_fibonacci(n_grid), radius)
+    S = args.sec3_starts
+    cst = torch.empty((B, S, 4), dtype=torch.float32, device=device)
+    quat = torch.empty((B, 4), dtype=torch.float32, device=device)
+    score = torch.empty((B,), dtype=torch.float32, device=device)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        bh.bh_expand(plan, vols, coeffs, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        bh.bh_candidates(plan, grid, tmpl, coeffs, w.stages[0], S, starts_out=cst, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        bh.bh_align_batch(plan, tmpl, coeffs, cst, w.stages, args.sec3_steps, quat_out=quat, score_out=score,
+                          stream=stream, newton=True)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    steps = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    torch.cuda.synchronize(device)
+    replicas.barrier()
+    for k in range(steps):
+        step(evs[k])
+        flush.zero_()
+    torch.cuda.synchronize(device)
+    replicas.barrier()
+    t = [sum(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(3)]
+    t = replicas.max_over_ranks(t, device)
+    q = quat.cpu().numpy().astype(np.float64)
+    qt_inv = w.q_true * np.array([1, -1, -1, -1])
+    ang = angle_deg(q, qt_inv)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    grid.destroy()
+    return {"value": world * B / (sum(t) / steps / 1e3), "unit": UNIT, "ms_per_step": sum(t) / steps,
+            "breakdown_ms_per_step": {"expand": t[0] / steps, "candidates": t[1] / steps, "newton": t[2] / steps},
+            "median_angle_vs_truth_deg": float(np.median(ang)), "frac_within_2deg": float(np.mean(ang < 2.0)),
+            "config": {"grid": f"super-Fibonacci {n_grid} rotations, neighbour radius {args.sec3_radius:g} deg",
+                       "candidate_band": w.stages[0], "candidates": S, "newton_steps_per_band": args.sec3_steps,
+                       "bands": w.stages},
+            "gpu_launches_per_step": 5}
 
 
 def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
@@ -447,6 +506,12 @@ def main():
     ap.add_argument("--starts-per-thread", type=int, default=2, help="starts per thread with --no-autotune")
     ap.add_argument("--distinct", type=int, default=0, help="generate only this many distinct phantoms and tile them")
     ap.add_argument("--refine", type=int, default=None, help="FP64 re-scoring of the K best starts (precision form)")
+    ap.add_argument("--sec3", type=int, default=None,
+                    help="also time the Sec. III protocol (candidates + Newton); default: on for batch32")
+    ap.add_argument("--sec3-grid", type=int, default=4608, help="rotation grid size for the candidate starts")
+    ap.add_argument("--sec3-radius", type=float, default=25.0, help="neighbour radius of the grid (degrees)")
+    ap.add_argument("--sec3-starts", type=int, default=4, help="candidate starts per subtomogram")
+    ap.add_argument("--sec3-steps", type=int, default=8, help="Newton steps per marching band")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -474,6 +539,8 @@ def main():
 
     if args.refine is None:
         args.refine = 4 if args.workload == "precision64" else 0
+    if args.sec3 is None:
+        args.sec3 = 1 if args.workload == "batch32" else 0
     if args.workload == "mixed":
         line = run_mixed(args, device)
         if rank == 0:
@@ -539,6 +606,8 @@ def main():
                                                             "align": f["t_aln"] / args.steps},
                                   "median_angle_vs_truth_deg": float(np.median(angle_deg(f["q"], qt_inv)))}
         line["accuracy"] = acc
+        if r.get("sec3"):
+            line["sec3_protocol"] = r["sec3"]
         if base is not None:
             line["cpu_baseline"] = base
         if world == 1 and args.serve_seconds > 0:

@@ -170,6 +170,18 @@ int bh_score_grad(const bh_plan* plan, const float* tmpl, const float* sub, int 
 int bh_energy(const bh_plan* plan, const float* tmpl, const float* sub, int B, int L, const int* tmpl_index,
               int n_templates, float* energy, void* stream);
 
+/*
+ * Score, gradient and Hessian of Eq. 2 (Newton steps, Sec. III) at S rotations per subtomogram, band L.
+ * The Hessian is the second derivative of S(R exp(eps.J)) at eps = 0 (body frame, symmetric),
+ * H_ij = -Re sum_l sum_{m,m'} xi^l_{mm'} [D^l(R) (J_i J_j + J_j J_i)/2]_{mm'}; it is evaluated through
+ * Euler-angle derivatives and set to zero within sin(beta) <= 1e-4 of the Euler chart's poles.
+ *   score  device, B * S floats;  grad  device, B * S * 3 floats or NULL
+ *   hess   device, B * S * 6 floats (xx, xy, xz, yy, yz, zz) or NULL
+ * Other arguments as bh_score_grad.
+ */
+int bh_score_hess(const bh_plan* plan, const float* tmpl, const float* sub, int B, const float* quats, int S,
+                  int L, float* score, float* grad, float* hess, void* stream);
+
 /* ------------------------------------------------------------------ alignment */
 typedef struct {
   int group;              /* lanes cooperating on one start: 0 = autotuned, else 1, 2, 4, 8 or 16 */
@@ -183,6 +195,12 @@ typedef struct {
                              score) at the last band with the d-recursion, seeds, phases and sums in
                              FP64 and select among them on the FP64 score (score_out then holds it,
                              rounded to float).  Needs start_quat_out and start_score_out.  0 = off */
+  int newton;             /* 0: gradient ascent (Sec. II-C).  1: damped Newton steps (Sec. III): per
+                             iteration, d = -H^{-1} g when -H is positive definite, else the gradient
+                             step pi/(2L) g/|g|; d clipped to length pi/L and scaled by a damping factor
+                             lam (1 at each stage start); the trial R exp(d.J) is accepted if it raises
+                             the score (lam <- min(1, 2 lam)), else lam <- lam/2.  One start per thread
+                             group (starts_per_thread 0 or 1); `group` 0 picks a default */
 } bh_align_opts;
 
 /*

@@ -21,7 +21,7 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
-           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad",
+           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
            "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_grid_create", "bh_grid_destroy", "bh_grid_info",
            "bh_grid_neighbors", "bh_candidates", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
@@ -41,7 +41,7 @@ class PlanOpts(ctypes.Structure):
 class AlignOpts(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int), ("tmpl_index", ctypes.c_void_p), ("n_templates", ctypes.c_int),
                 ("start_quat_out", ctypes.c_void_p), ("start_score_out", ctypes.c_void_p),
-                ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int)]
+                ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int), ("newton", ctypes.c_int)]
 
 
 _lib = None
@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         L.bh_expand.argtypes = [vp, vp, i, vp, vp]
         L.bh_expand_noalloc.argtypes = [vp, vp, i, vp, vp]
         L.bh_score_grad.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp]
+        L.bh_score_hess.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp, vp]
         L.bh_align_batch.argtypes = [vp, vp, vp, i, vp, i, vp, i, i, vp, vp, ctypes.POINTER(AlignOpts), vp]
         L.bh_grid_create.argtypes = [ctypes.POINTER(vp), vp, i, d]
         L.bh_grid_destroy.argtypes = [vp]
@@ -190,10 +191,25 @@ def bh_score_grad(plan: Plan, tmpl, sub, quats, L: int, with_grad: bool = True, 
     return score, grad
 
 
+def bh_score_hess(plan: Plan, tmpl, sub, quats, L: int, stream=None):
+    """Score (B,S), gradient (B,S,3) and Hessian (B,S,3,3) at band L."""
+    import torch
+    B, S = quats.shape[0], quats.shape[1]
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    _need(quats, "torch.float32", B * S * 4, "quats")
+    score = torch.empty((B, S), dtype=torch.float32, device=sub.device)
+    grad = torch.empty((B, S, 3), dtype=torch.float32, device=sub.device)
+    h6 = torch.empty((B, S, 6), dtype=torch.float32, device=sub.device)
+    _check(lib().bh_score_hess(plan.handle, _ptr(tmpl), _ptr(sub), B, _ptr(quats), S, L, _ptr(score), _ptr(grad),
+                               _ptr(h6), _stream(stream)), "bh_score_hess")
+    idx = torch.tensor([[0, 1, 2], [1, 3, 4], [2, 4, 5]], device=sub.device)
+    return score, grad, h6[..., idx]
+
+
 # ------------------------------------------------------------------ alignment
 def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
                    n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None,
-                   refine_fp64: int = 0, starts_per_thread: int = 0):
+                   refine_fp64: int = 0, starts_per_thread: int = 0, newton: bool = False):
     """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
     import torch
     B, S = starts.shape[0], starts.shape[1]
@@ -208,6 +224,7 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     o.group = group
     o.starts_per_thread = starts_per_thread
     o.refine_fp64 = refine_fp64
+    o.newton = int(bool(newton))
     sq = ss = None
     if per_start or refine_fp64:
         sq = torch.empty((B, S, 4), dtype=torch.float32, device=dev)

@@ -46,7 +46,8 @@ namespace {
 constexpr int kBinStride = 2 * kMaxL + 1;
 
 // Per-band constants of the rescaled recursion, read with a warp-uniform index (every lane of a warp
-// steps through the same l): l >= 2: (1/(l(l-1)), 1/((l-1)^2 (2l-1)(2l-3)), (l-1)^2, 0); zero below.
+// steps through the same l): l >= 2: (1/(l(l-1)), 1/((l-1)^2 (2l-1)(2l-3)), (l-1)^2, l(l+1)); below:
+// (0, 0, 0, l(l+1)).
 __constant__ float4 c_ecoef[kMaxL + 2];
 
 constexpr int kMaxStages = 8;
@@ -72,6 +73,7 @@ struct AlignArgs {
   float4* start_quat_out;
   float* start_score_out;
   float* grad_out;  // score kernel: [B][S][3]
+  float* hess_out;  // score kernel: [B][S][6] (xx, xy, xz, yy, yz, zz) or NULL
   double* score64_out;  // refine kernel: [B] FP64 score of the selected start (may be NULL)
 };
 
@@ -291,6 +293,247 @@ __device__ __forceinline__ Eval eval_one(const float4* __restrict__ tab, int Lb,
   return e[0];
 }
 
+// Score only (no gradient) of C rotations at band L, one lane per rotation: the d recursion without its
+// beta derivative, for grid evaluations.
+template <int C>
+__device__ void eval_scores(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C],
+                            const float* __restrict__ lbin, float (&out)[C]) {
+  float xb[C], lcc[C], lss[C];
+  float2 R1[C], R2[C], Ed2[C], Wrow[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
+    const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+    const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+    const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+    xb[j] = (cb - sb) * (cb + sb);
+    lcc[j] = log2f(fmaxf(cb, 1e-30f));
+    lss[j] = log2f(fmaxf(sb, 1e-30f));
+    const float2 Es = cconj(es);
+    R1[j] = cmul(Es, ed);
+    R2[j] = cmul(Es, cconj(ed));
+    const float2 Ed = cconj(ed);
+    Ed2[j] = cmul(Ed, Ed);
+    Wrow[j] = make_float2(1.f, 0.f);
+    out[j] = 0.f;
+  }
+  for (int m = 0; m <= L; ++m) {
+    const int w = 2 * m + 1;
+    const float4* rowp = tab + tab_base(m, Lb);
+    const float fm2 = (float)(m * m);
+    float2 P1[C], P2[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      // n = -m: phases Es^0 ed^{-m}... as in eval_rotations with qg = 0: P1 = Wrow, P2 = conj(Wrow)
+      P1[j] = Wrow[j];
+      P2[j] = cconj(Wrow[j]);
+    }
+    for (int n = -m; n <= m; ++n) {
+      const float lb = __ldg(lbin + m * kBinStride + m + n);
+      const float fa = (float)(m + n), fd = (float)(m - n);
+      const bool odd = (m - n) & 1;
+      const float4* ep = rowp + (n + m);
+      const float4 xv = *ep;
+      float e1[C], e2[C], a1r[C], a1i[C], a2r[C], a2i[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        float d = exp2f(lb + fa * lcc[j] + fd * lss[j]);
+        d = odd ? -d : d;
+        a1r[j] = d * xv.x; a1i[j] = d * xv.y; a2r[j] = d * xv.z; a2i[j] = d * xv.w;
+        e1[j] = d;
+        e2[j] = 0.f;
+      }
+      const float mn = (float)(m * n), fn2 = (float)(n * n);
+      for (int l = m + 1; l <= L; ++l) {
+        const float4 k0 = c_ecoef[l];
+        ep += w;
+        const float4 X = *ep;
+        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const float en = fmaf(fmaf(-mn, k0.x, xb[j]), e1[j], -g0 * e2[j]);
+          a1r[j] = fmaf(en, X.x, a1r[j]); a1i[j] = fmaf(en, X.y, a1i[j]);
+          a2r[j] = fmaf(en, X.z, a2r[j]); a2i[j] = fmaf(en, X.w, a2i[j]);
+          e2[j] = e1[j];
+          e1[j] = en;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        out[j] += (P1[j].x * a1r[j] - P1[j].y * a1i[j]) + (P2[j].x * a2r[j] - P2[j].y * a2i[j]);
+        P1[j] = cmul(P1[j], R1[j]);
+        P2[j] = cmul(P2[j], R2[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) Wrow[j] = cmul(Wrow[j], Ed2[j]);
+  }
+}
+
+struct EvalH {
+  float S, gx, gy, gz;
+  float hxx, hxy, hxz, hyy, hyz, hzz;  // symmetric body-frame Hessian
+};
+
+// Score, body-frame gradient and Hessian (FP32) of one rotation at band L (Newton steps, Sec. III).  The
+// evaluation follows eval_rotations with C = 1 and adds the second Euler-angle derivatives: along alpha and
+// gamma the orbit terms only pick up factors of m and n; the second beta derivative comes from the Wigner
+// d equation d'' = -cot(b) d' - [l(l+1) - (m^2 + n^2 - 2mn cos b)/sin^2 b] d, which needs one more sum,
+// Lambda = sum_l l(l+1) e_l X_l, per orbit.  The body-frame Hessian is the symmetrised X_i X_j S of the
+// vector fields X_i of the gradient.
+template <int G>
+__device__ EvalH eval_hess(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg,
+                           const float* __restrict__ lbin) {
+  const float w = q.x, x = q.y, y = q.z, z = q.w;
+  const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+  const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+  const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+  const float xb = (cb - sb) * (cb + sb), sinb = 2.f * cb * sb;
+  const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
+  const float lcc = log2f(cbc), lss = log2f(sbc), rcs = cbc / sbc, rsc = sbc / cbc;
+  const float2 Es = cconj(es);
+  const float2 EsG = cpow(Es, G), edG = cpow(ed, G);
+  const float2 R1 = cmul(EsG, edG), R2 = cmul(EsG, cconj(edG));
+  const float2 Ed = cconj(ed);
+  const float2 Ed2 = cmul(Ed, Ed);
+  const float2 Uq = cpow(Es, qg);
+  float2 Wrow = cpow(ed, qg);
+  float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
+  float Saa = 0.f, Sab = 0.f, Sag = 0.f, Sbg = 0.f, Sgg = 0.f, Sk = 0.f, SL = 0.f;
+  for (int m = 0; m <= L; ++m) {
+    const int wd = 2 * m + 1;
+    const float4* rowp = tab + tab_base(m, Lb);
+    const float fm2 = (float)(m * m), fm = (float)m;
+    float2 P1 = cmul(Uq, Wrow), P2 = cmul(Uq, cconj(Wrow));
+    float rS = 0.f, rI1 = 0.f, rI2 = 0.f, rN1 = 0.f, rN2 = 0.f, rB = 0.f;
+    float hU1 = 0.f, hU2 = 0.f, hUn1 = 0.f, hUn2 = 0.f, hUnn1 = 0.f, hUnn2 = 0.f;
+    float hY1 = 0.f, hY2 = 0.f, hYn1 = 0.f, hYn2 = 0.f, hL = 0.f;
+    for (int n = qg - m; n <= m; n += G) {
+      const float lb = __ldg(lbin + m * kBinStride + m + n);
+      const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
+      const float4* ep = rowp + (n + m);
+      const float4 xv = *ep;
+      float d = exp2f(lb + fa * lcc + fd * lss);
+      d = ((m - n) & 1) ? -d : d;
+      const float dp = 0.5f * d * (fd * rcs - fa * rsc);
+      const float ll0 = (float)(m * (m + 1));
+      float a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
+      float b1r = dp * xv.x, b1i = dp * xv.y, b2r = dp * xv.z, b2i = dp * xv.w;
+      float q1r = ll0 * a1r, q1i = ll0 * a1i, q2r = ll0 * a2r, q2i = ll0 * a2i;
+      float e1 = d, e2 = 0.f, p1 = dp, p2 = 0.f;
+      const float mn = (float)(m * n), fn2 = (float)(n * n);
+      for (int l = m + 1; l <= L; ++l) {
+        const float4 k0 = c_ecoef[l];
+        ep += wd;
+        const float4 X = *ep;
+        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
+        const float t_ = fmaf(-mn, k0.x, xb);
+        const float en = fmaf(t_, e1, -g0 * e2);
+        const float pn = fmaf(t_, p1, -fmaf(sinb, e1, g0 * p2));
+        a1r = fmaf(en, X.x, a1r); a1i = fmaf(en, X.y, a1i); a2r = fmaf(en, X.z, a2r); a2i = fmaf(en, X.w, a2i);
+        b1r = fmaf(pn, X.x, b1r); b1i = fmaf(pn, X.y, b1i); b2r = fmaf(pn, X.z, b2r); b2i = fmaf(pn, X.w, b2i);
+        const float el = k0.w * en;
+        q1r = fmaf(el, X.x, q1r); q1i = fmaf(el, X.y, q1i); q2r = fmaf(el, X.z, q2r); q2i = fmaf(el, X.w, q2i);
+        e2 = e1; e1 = en; p2 = p1; p1 = pn;
+      }
+      const float z1r = P1.x * a1r - P1.y * a1i, z1i = P1.x * a1i + P1.y * a1r;
+      const float z2r = P2.x * a2r - P2.y * a2i, z2i = P2.x * a2i + P2.y * a2r;
+      const float y1r = P1.x * b1r - P1.y * b1i, y1i = P1.x * b1i + P1.y * b1r;
+      const float y2r = P2.x * b2r - P2.y * b2i, y2i = P2.x * b2i + P2.y * b2r;
+      rS += z1r + z2r;
+      rI1 += z1i;
+      rI2 += z2i;
+      rN1 = fmaf(fn, z1i, rN1);
+      rN2 = fmaf(fn, z2i, rN2);
+      rB += y1r + y2r;
+      hU1 += z1r;
+      hU2 += z2r;
+      hUn1 = fmaf(fn, z1r, hUn1);
+      hUn2 = fmaf(fn, z2r, hUn2);
+      hUnn1 = fmaf(fn2, z1r, hUnn1);
+      hUnn2 = fmaf(fn2, z2r, hUnn2);
+      hY1 += y1i;
+      hY2 += y2i;
+      hYn1 = fmaf(fn, y1i, hYn1);
+      hYn2 = fmaf(fn, y2i, hYn2);
+      hL += (P1.x * q1r - P1.y * q1i) + (P2.x * q2r - P2.y * q2i);
+      P1 = cmul(P1, R1);
+      P2 = cmul(P2, R2);
+    }
+    S += rS;
+    Sa += fm * rI1 + rN2;
+    Sg += rN1 + fm * rI2;
+    Sb += rB;
+    Saa -= fm2 * hU1 + hUnn2;
+    Sgg -= hUnn1 + fm2 * hU2;
+    Sag -= fm * (hUn1 + hUn2);
+    Sab += fm * hY1 + hYn2;
+    Sbg += hYn1 + fm * hY2;
+    Sk += fm2 * (hU1 + hU2) + (hUnn1 + hUnn2) - 2.f * xb * fm * (hUn1 + hUn2);
+    SL += hL;
+    Wrow = cmul(Wrow, Ed2);
+  }
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    S += __shfl_xor_sync(0xffffffffu, S, o);
+    Sa += __shfl_xor_sync(0xffffffffu, Sa, o);
+    Sb += __shfl_xor_sync(0xffffffffu, Sb, o);
+    Sg += __shfl_xor_sync(0xffffffffu, Sg, o);
+    Saa += __shfl_xor_sync(0xffffffffu, Saa, o);
+    Sab += __shfl_xor_sync(0xffffffffu, Sab, o);
+    Sag += __shfl_xor_sync(0xffffffffu, Sag, o);
+    Sbg += __shfl_xor_sync(0xffffffffu, Sbg, o);
+    Sgg += __shfl_xor_sync(0xffffffffu, Sgg, o);
+    Sk += __shfl_xor_sync(0xffffffffu, Sk, o);
+    SL += __shfl_xor_sync(0xffffffffu, SL, o);
+  }
+  const float2 eg = cmul(es, cconj(ed));  // (cos gamma, sin gamma)
+  const float cG = eg.x, sG = eg.y;
+  EvalH r;
+  r.S = S;
+  if (!(sinb > 1e-4f)) {  // Euler chart singular: gradient only along gamma, no curvature information
+    const float Q = 0.f;
+    r.gx = Sb * sG + Q * cG;
+    r.gy = Sb * cG - Q * sG;
+    r.gz = Sg;
+    r.hxx = r.hxy = r.hxz = r.hyy = r.hyz = r.hzz = 0.f;
+    return r;
+  }
+  const float isb = 1.f / sinb, isb2 = isb * isb;
+  const float Q = (xb * Sg - Sa) * isb;
+  r.gx = Sb * sG + Q * cG;
+  r.gy = Sb * cG - Q * sG;
+  r.gz = Sg;
+  const float Sbb = -xb * isb * Sb + Sk * isb2 - SL;
+  // X_i = v_i . (d_alpha, d_beta, d_gamma); X_i X_j S = v_i^T E v_j + (b_i d_beta v_j + c_i d_gamma v_j) . grad
+  const float v[3][3] = {{-cG * isb, sG, xb * cG * isb}, {sG * isb, cG, -xb * sG * isb}, {0.f, 0.f, 1.f}};
+  const float dbv[3][3] = {{cG * xb * isb2, 0.f, -cG * isb2}, {-sG * xb * isb2, 0.f, sG * isb2}, {0.f, 0.f, 0.f}};
+  const float dgv[3][3] = {{v[1][0], v[1][1], v[1][2]}, {-v[0][0], -v[0][1], -v[0][2]}, {0.f, 0.f, 0.f}};
+  const float E[3][3] = {{Saa, Sab, Sag}, {Sab, Sbb, Sbg}, {Sag, Sbg, Sgg}};
+  const float gr[3] = {Sa, Sb, Sg};
+  float XX[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float Ev[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Ev[k] = E[k][0] * v[i][0] + E[k][1] * v[i][1] + E[k][2] * v[i][2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float t = v[j][0] * Ev[0] + v[j][1] * Ev[1] + v[j][2] * Ev[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t = fmaf(v[i][1] * dbv[j][k] + v[i][2] * dgv[j][k], gr[k], t);
+      XX[i][j] = t;
+    }
+  }
+  r.hxx = XX[0][0];
+  r.hyy = XX[1][1];
+  r.hzz = XX[2][2];
+  r.hxy = 0.5f * (XX[0][1] + XX[1][0]);
+  r.hxz = 0.5f * (XX[0][2] + XX[2][0]);
+  r.hyz = 0.5f * (XX[1][2] + XX[2][1]);
+  return r;
+}
+
 __device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p) {
   if (!a.tmpl_index) return a.tmpl;
   int t = a.tmpl_index[p];
@@ -384,6 +627,133 @@ __global__ void __launch_bounds__(512, 1) k_score(const AlignArgs a, int L) {
       g[1] = r.gy;
       g[2] = r.gz;
     }
+  }
+}
+
+// Score, gradient and Hessian at given rotations; one CTA per subtomogram.
+template <int G>
+__global__ void __launch_bounds__(512, 1) k_score_hess(const AlignArgs a, int L) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  const int s = threadIdx.x / G, qg = threadIdx.x % G;
+  const bool active = s < a.S;
+  const int se = active ? s : s % a.S;
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
+  __syncthreads();
+  const EvalH r = eval_hess<G>(smem_tab, a.Lb, L, qnormalize(a.starts[(size_t)p * a.S + se]), qg, a.lbin);
+  if (active && qg == 0) {
+    const size_t o = (size_t)p * a.S + s;
+    a.score_out[o] = r.S;
+    if (a.grad_out) {
+      a.grad_out[o * 3 + 0] = r.gx;
+      a.grad_out[o * 3 + 1] = r.gy;
+      a.grad_out[o * 3 + 2] = r.gz;
+    }
+    if (a.hess_out) {
+      float* h = a.hess_out + o * 6;
+      h[0] = r.hxx; h[1] = r.hxy; h[2] = r.hxz; h[3] = r.hyy; h[4] = r.hyz; h[5] = r.hzz;
+    }
+  }
+}
+
+// Newton direction d = -H^{-1} g when -H is positive definite (Cholesky pivots > 0), else the gradient step
+// h0 g/|g|; clipped to length hmax.  Returns the length of d.
+__device__ __forceinline__ float newton_dir(const EvalH& e, float gn, float h0, float hmax, float d[3]) {
+  bool pd = false;
+  const float a11 = -e.hxx;
+  if (a11 > 0.f) {
+    const float l11 = sqrtf(a11), l21 = -e.hxy / l11, l31 = -e.hxz / l11;
+    const float a22 = -e.hyy - l21 * l21;
+    if (a22 > 0.f) {
+      const float l22 = sqrtf(a22), l32 = (-e.hyz - l31 * l21) / l22;
+      const float a33 = -e.hzz - l31 * l31 - l32 * l32;
+      if (a33 > 0.f) {
+        pd = true;
+        const float l33 = sqrtf(a33);
+        // (-H) d = g:  L y = g, L^T d = y
+        const float y1 = e.gx / l11, y2 = (e.gy - l21 * y1) / l22, y3 = (e.gz - l31 * y1 - l32 * y2) / l33;
+        d[2] = y3 / l33;
+        d[1] = (y2 - l32 * d[2]) / l22;
+        d[0] = (y1 - l21 * d[1] - l31 * d[2]) / l11;
+      }
+    }
+  }
+  if (!pd) {
+    const float sc = gn > 0.f ? h0 / gn : 0.f;
+    d[0] = sc * e.gx;
+    d[1] = sc * e.gy;
+    d[2] = sc * e.gz;
+  }
+  float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (dn > hmax) {
+    const float sc = hmax / dn;
+    d[0] *= sc;
+    d[1] *= sc;
+    d[2] *= sc;
+    dn = hmax;
+  }
+  return dn;
+}
+
+// Damped Newton iteration with frequency marching (Sec. III); one CTA per subtomogram, NT = roundup(S*G, 32).
+template <int G, int NT>
+__global__ void __launch_bounds__(NT, min_blocks(NT)) k_newton(const AlignArgs a) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  const int s = threadIdx.x / G, qg = threadIdx.x % G;
+  const bool active = s < a.S;
+  const int se = active ? s : s % a.S;
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+              blockDim.x);
+  __syncthreads();
+  float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
+  EvalH cur;
+  cur.S = 0.f;
+  for (int st = 0; st < a.nstages; ++st) {
+    const int L = a.stages[st];
+    const float hmax = 3.14159265358979f / (float)L, h0 = 0.5f * hmax;
+    float lam = 1.f;
+    cur = eval_hess<G>(smem_tab, a.Lb, L, q, qg, a.lbin);
+    for (int t = 0; t < a.steps; ++t) {
+      const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
+      const bool stop = !(gn > 1e-12f * fabsf(cur.S));
+      float d[3];
+      const float dl = newton_dir(cur, gn, h0, hmax, d);  // |d| before damping
+      const float dn = lam * dl;                          // rotation angle of the trial step
+      const float inv = (stop || !(dl > 0.f)) ? 0.f : 1.f / dl;
+      float sh, ch;
+      sincosf(stop ? 0.f : 0.5f * dn, &sh, &ch);
+      const float4 dq = make_float4(ch, sh * d[0] * inv, sh * d[1] * inv, sh * d[2] * inv);
+      const float4 qt = qnormalize(qmul(q, dq));
+      const EvalH tr = eval_hess<G>(smem_tab, a.Lb, L, qt, qg, a.lbin);
+      if (!stop) {
+        if (tr.S > cur.S) {
+          q = qt;
+          cur = tr;
+          lam = fminf(1.f, 2.f * lam);
+        } else {
+          lam *= 0.5f;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float* sS = reinterpret_cast<float*>(smem_tab);
+  float4* sQ = reinterpret_cast<float4*>(sS + ((a.S + 3) & ~3));
+  if (active && qg == 0) {
+    sS[s] = cur.S;
+    sQ[s] = q;
+    if (a.start_quat_out) a.start_quat_out[(size_t)p * a.S + s] = q;
+    if (a.start_score_out) a.start_score_out[(size_t)p * a.S + s] = cur.S;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int j = 1; j < a.S; ++j)
+      if (sS[j] > sS[best]) best = j;
+    a.quat_out[p] = sQ[best];
+    a.score_out[p] = sS[best];
   }
 }
 
@@ -714,6 +1084,55 @@ int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t
   }
 }
 
+template <int G, int NT>
+int launch_newton_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
+  static std::atomic<int> have{0};
+  int st = ensure_smem(k_newton<G, NT>, have, smem);
+  if (st != BH_OK) return st;
+  k_newton<G, NT><<<a.B, NT, smem, stream>>>(a);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+template <int G>
+int launch_newton_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stream) {
+  const int threads = round_up(a.S * G, 32);
+  const size_t sel = (size_t)((a.S + 3) & ~3) * sizeof(float) + (size_t)a.S * sizeof(float4);
+  const size_t smem = std::max(table_bytes(a.Lb), score_only ? (size_t)16 : sel);
+  if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
+  if (score_only) {
+    static std::atomic<int> have{0};
+    int st = ensure_smem(k_score_hess<G>, have, smem);
+    if (st != BH_OK) return st;
+    k_score_hess<G><<<a.B, threads, smem, stream>>>(a, L);
+    BH_CHECK_LAUNCH();
+    return BH_OK;
+  }
+  switch (threads) {
+    case 32: return launch_newton_nt<G, 32>(a, smem, stream);
+    case 64: return launch_newton_nt<G, 64>(a, smem, stream);
+    case 96:
+    case 128: return launch_newton_nt<G, 128>(a, smem, stream);
+    case 160:
+    case 192:
+    case 224:
+    case 256: return launch_newton_nt<G, 256>(a, smem, stream);
+    default: return launch_newton_nt<G, 512>(a, smem, stream);
+  }
+}
+
+// Newton iteration (or, score_only, the score/gradient/Hessian evaluation at band L) with G lanes per start.
+int launch_newton(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t stream) {
+  switch (G) {
+    case 1: return launch_newton_g<1>(a, score_only, L, stream);
+    case 2: return launch_newton_g<2>(a, score_only, L, stream);
+    case 4: return launch_newton_g<4>(a, score_only, L, stream);
+    case 8: return launch_newton_g<8>(a, score_only, L, stream);
+    case 16: return launch_newton_g<16>(a, score_only, L, stream);
+    default: return fail(BH_ERR_ARG, "group %d not in {1,2,4,8,16}", G);
+  }
+}
+
 template <int G>
 int launch_refine_g(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
   const int threads = round_up(K * G, 32);
@@ -763,11 +1182,11 @@ int align_init_constants() {
   float4 ec[kMaxL + 2];
   for (int l = 0; l < kMaxL + 2; ++l) {
     if (l < 2) {
-      ec[l] = make_float4(0.f, 0.f, 0.f, 0.f);
+      ec[l] = make_float4(0.f, 0.f, 0.f, (float)(l * (l + 1)));
     } else {
       const double a = (double)(l - 1) * (l - 1);
       ec[l] = make_float4((float)(1.0 / ((double)l * (l - 1))), (float)(1.0 / (a * (2.0 * l - 1.0) * (2.0 * l - 3.0))),
-                          (float)a, 0.f);
+                          (float)a, (float)(l * (l + 1)));
     }
   }
   BH_CUDA_TRY(cudaMemcpyToSymbol(c_ecoef, ec, sizeof(ec)));
@@ -809,6 +1228,30 @@ extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* s
   a.grad_out = grad;
   int G = default_group(S, L);
   return launch_align(a, G, true, L, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int bh_score_hess(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* quats, int S,
+                             int L, float* score, float* grad, float* hess, void* stream) {
+  clear_error();
+  int st = check_common(p, tmpl, sub, B, quats, S);
+  if (st != BH_OK) return st;
+  if (L < 0 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 0..%d", L, p->Lmax);
+  if (B == 0) return BH_OK;
+  if (!score) return fail(BH_ERR_ARG, "score is NULL");
+  AlignArgs a{};
+  a.lay = p->layout;
+  a.tmpl = reinterpret_cast<const float2*>(tmpl);
+  a.sub = reinterpret_cast<const float2*>(sub);
+  a.B = B;
+  a.starts = reinterpret_cast<const float4*>(quats);
+  a.S = S;
+  a.Lb = L;
+  a.P = p->d_P;
+  a.lbin = p->d_lbin;
+  a.score_out = score;
+  a.grad_out = grad;
+  a.hess_out = hess;
+  return launch_newton(a, default_group(S, L), true, L, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* starts, int S,
@@ -867,7 +1310,13 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     }
   }
   if (C == 0) C = 1;
-  if (C == 2) {
+  if (opts && opts->newton) {
+    if (opts->starts_per_thread > 1) return fail(BH_ERR_ARG, "Newton steps run one start per thread group");
+    if (opts->group == 0) G = default_group(S, a.Lb);
+    if (round_up(S * G, 32) > kMaxThreads)
+      return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
+    st = launch_newton(a, G, false, 0, static_cast<cudaStream_t>(stream));
+  } else if (C == 2) {
     if (round_up((S / 2) * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S/2*group = %d exceeds %d threads", (S / 2) * G, kMaxThreads);
     st = launch_align_c2(a, G, static_cast<cudaStream_t>(stream));
@@ -1151,21 +1600,25 @@ struct GridArgs {
   float* score_out;    // [B][n] or NULL
 };
 
+constexpr int kSelectRounds = 64;  // up to this many candidates: S rounds of a block-wide argmax; above: sort
+
 // One CTA per subtomogram: Eq. 2 at band L on every grid rotation (orbit table of band L in shared memory),
-// local-maximum flags from the neighbour lists, a bitonic sort of the keys, the first S grid rotations out.
+// local-maximum flags from the neighbour lists, then the S highest keys, either by S rounds of a block-wide
+// argmax (S <= kSelectRounds) or by a bitonic sort of next_pow2(n) keys.
 template <int C>
 __global__ void __launch_bounds__(kCandThreads, 2) k_grid_candidates(const AlignArgs a, const GridArgs g) {
   extern __shared__ float4 smem_tab[];
+  __shared__ unsigned long long wbest[kCandThreads / 32];
   const int p = blockIdx.x;
   const int ntab = tab_base(a.Lb + 1, a.Lb);
+  const bool sort = a.S > kSelectRounds;
+  const int nkeys = sort ? g.npow2 : g.n;
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_tab + ntab);
-  unsigned* flag = reinterpret_cast<unsigned*>(key + g.npow2);
   build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
               blockDim.x);
-  for (int w = threadIdx.x; w < (g.npow2 >> 5); w += blockDim.x) flag[w] = 0u;
-  for (int i = g.n + threadIdx.x; i < g.npow2; i += blockDim.x) key[i] = 0ull;  // padding ranks last
+  for (int i = g.n + threadIdx.x; i < nkeys; i += blockDim.x) key[i] = 0ull;  // padding ranks last
   __syncthreads();
-  // every thread runs the same number of passes (the evaluation shuffles within warps)
+  // one lane per grid rotation, C rotations per thread and pass
   const int per_pass = blockDim.x * C;
   const int passes = (g.n + per_pass - 1) / per_pass;
   for (int it = 0; it < passes; ++it) {
@@ -1176,27 +1629,68 @@ __global__ void __launch_bounds__(kCandThreads, 2) k_grid_candidates(const Align
       idx[j] = it * per_pass + j * blockDim.x + threadIdx.x;
       q[j] = qnormalize(g.q[idx[j] < g.n ? idx[j] : g.n - 1]);
     }
-    Eval e[C];
-    eval_rotations<1, C>(smem_tab, a.Lb, g.L, q, 0, a.lbin, e);
+    float e[C];
+    eval_scores<C>(smem_tab, a.Lb, g.L, q, a.lbin, e);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       if (idx[j] < g.n) {
-        key[idx[j]] = grid_key(e[j].S, idx[j]);
-        if (g.score_out) g.score_out[(size_t)p * g.n + idx[j]] = e[j].S;
+        key[idx[j]] = grid_key(e[j], idx[j]);
+        if (g.score_out) g.score_out[(size_t)p * g.n + idx[j]] = e[j];
       }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+  // local maxima: thread t owns grid points t + k * blockDim (k < n / blockDim <= 64), flags in a bit mask
+  unsigned long long fmask = 0ull;
+  for (int i = threadIdx.x, k = 0; i < g.n; i += blockDim.x, ++k) {
     const unsigned long long ki = key[i];
     bool mx = true;
     for (int e = g.off[i], e1 = g.off[i + 1]; e < e1 && mx; ++e) mx = key[g.nbr[e]] < ki;
-    if (mx) atomicOr(flag + (i >> 5), 1u << (i & 31));
+    if (mx) fmask |= 1ull << k;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < g.n; i += blockDim.x)
-    if ((flag[i >> 5] >> (i & 31)) & 1u) key[i] |= 1ull << 63;
+  for (int i = threadIdx.x, k = 0; i < g.n; i += blockDim.x, ++k)
+    if ((fmask >> k) & 1ull) key[i] |= 1ull << 63;
   __syncthreads();
+  if (!sort) {
+    unsigned long long mine = 0ull;
+    int pos = -1;
+    for (int i = threadIdx.x; i < g.n; i += blockDim.x)
+      if (key[i] > mine) {
+        mine = key[i];
+        pos = i;
+      }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = 0; s < a.S; ++s) {
+      unsigned long long v = mine;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+      }
+      if (lane == 0) wbest[warp] = v;
+      __syncthreads();
+      unsigned long long best = wbest[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wbest[w] > best ? wbest[w] : best;
+      if (threadIdx.x == 0) {
+        const int i = 0x7FFFFFFF - (int)(best & 0x7FFFFFFFull);
+        g.starts_out[(size_t)p * a.S + s] = g.q[i];
+        if (g.index_out) g.index_out[(size_t)p * a.S + s] = i;
+      }
+      if (pos >= 0 && mine == best) {  // keys are unique: exactly one owner; it drops the key and rescans
+        key[pos] = 0ull;
+        mine = 0ull;
+        pos = -1;
+        for (int i = threadIdx.x; i < g.n; i += blockDim.x)
+          if (key[i] > mine) {
+            mine = key[i];
+            pos = i;
+          }
+      }
+      __syncthreads();
+    }
+    return;
+  }
   // bitonic sort, descending
   for (int k = 2; k <= g.npow2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -1218,8 +1712,8 @@ __global__ void __launch_bounds__(kCandThreads, 2) k_grid_candidates(const Align
   }
 }
 
-size_t grid_smem(int L, int npow2) {
-  return table_bytes(L) + (size_t)npow2 * 8 + (size_t)(npow2 / 32) * 4;
+size_t grid_smem(int L, int n, int npow2, int S) {
+  return table_bytes(L) + (size_t)(S > kSelectRounds ? npow2 : n) * 8;
 }
 }  // namespace
 }  // namespace bh
@@ -1308,7 +1802,7 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
   int dev = 0;
   BH_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != grid->device) return fail(BH_ERR_ARG, "grid lives on device %d, current device is %d", grid->device, dev);
-  const size_t smem = grid_smem(L, grid->npow2);
+  const size_t smem = grid_smem(L, grid->n, grid->npow2, S);
   if (smem > 232448) return fail(BH_ERR_ARG, "band %d with %d grid points needs %zu bytes of shared memory", L, grid->n, smem);
   AlignArgs a{};
   a.lay = p->layout;

@@ -366,3 +366,91 @@ def test_shift_search_matches_oracle(dev):
         ref = align.align_shifts(Bs, t, vols[b].astype(np.float64), shifts, starts[b].astype(np.float64), [2, 4, 8], 30)
         assert ref.shift == idx[b]
         assert math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), ref.q)) < 0.1
+
+
+# ---------------------------------------------------------------------------- Newton steps (Sec. III)
+@pytest.mark.parametrize("L", [1, 2, 5, 8])
+def test_score_hess_matches_oracle(dev, L):
+    """Hessian tolerance 1e-4 (L+1)^2 ||t|| ||f|| (second derivatives carry up to l^2), at sin(beta) > 0.2: the
+    Euler-chart terms grow like 1/sin^2(beta) towards the poles."""
+    Bs = basis_for(16, 8)
+    rng = np.random.default_rng(70 + L)
+    c = realish_coeffs(Bs, rng, 3)
+    t, subs = c[0], c[1:]
+    B, S = 2, 9
+    quats = []
+    for _ in range(B):
+        qs = [q for q in off_pole_quats(rng, 60) if 2 * math.hypot(q[1], q[2]) * math.hypot(q[0], q[3]) > 0.2]
+        quats.append(qs[:S])
+    quats = np.array(quats)
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    sc, gr, H = bh.bh_score_hess(p, to_f32(t).to(dev), to_f32(subs).to(dev),
+                                 torch.from_numpy(quats.astype(np.float32)).to(dev), L)
+    sc, gr, H = sc.cpu().numpy(), gr.cpu().numpy(), H.cpu().numpy()
+    o = Bs.offsets[L + 1]
+    for b in range(B):
+        xi = align.build_xi(Bs, t, subs[b], L)
+        scale = np.linalg.norm(t[:o]) * np.linalg.norm(subs[b][:o])
+        for s in range(S):
+            q = quats[b, s].astype(np.float32).astype(np.float64)
+            S_ref, g_ref, H_ref = align.score_grad_hess(xi, q, L)
+            assert abs(sc[b, s] - S_ref) <= 1e-4 * scale
+            assert np.max(np.abs(gr[b, s] - g_ref)) <= 1e-4 * (L + 1) * scale
+            assert np.max(np.abs(H[b, s] - H_ref)) <= 1e-4 * (L + 1) ** 2 * scale, (b, s, H[b, s], H_ref)
+
+
+def test_newton_pair16_matches_oracle(dev):
+    """Plain method's pair (16^3, l <= 8, 2-4-8, 8 starts) with Newton steps (15 per stage): same optimum as the
+    oracle's Newton iteration from the same starts, and R_true^{-1} recovered."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = align.align_particle(Bs, t, f, w.starts[0].astype(np.float64), w.stages, 15, method="newton")
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    for group in (1, 4):
+        q, s = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev), torch.from_numpy(w.starts).to(dev),
+                                 w.stages, 15, group=group, newton=True)
+        q = q.cpu().numpy()[0].astype(np.float64)
+        q /= np.linalg.norm(q)
+        assert math.degrees(wigner.geodesic_angle(q, ref.q)) < 0.1
+        assert abs(float(s[0]) - ref.score) < 1e-4 * abs(ref.score)
+        assert math.degrees(wigner.geodesic_angle(q, wigner.quat_conj(w.q_true[0]))) < 3.0
+
+
+def test_newton_exact_rotation_converges(dev):
+    """Exactly rotated coefficients: Newton steps from uniform starts reach R^{-1} to FP32 accuracy."""
+    Bs = basis_for(16, 8)
+    rng = np.random.default_rng(81)
+    c = realish_coeffs(Bs, rng, 1)[0]
+    qs = synth.uniform_quaternions(rng, 4)
+    F = np.stack([align.rotate_coeffs(Bs, c, q) for q in qs])
+    starts = np.stack([synth.uniform_quaternions(rng, 8) for _ in range(4)]).astype(np.float32)
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    q, s = bh.bh_align_batch(p, to_f32(c).to(dev), to_f32(F).to(dev), torch.from_numpy(starts).to(dev), [2, 4, 8], 12,
+                             newton=True)
+    q = q.cpu().numpy().astype(np.float64)
+    for b in range(4):
+        assert math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), wigner.quat_conj(qs[b]))) < 0.02
+
+
+@pytest.mark.slow
+def test_newton_batch32_sample(dev):
+    """1024 x 32^3 workload shape with Newton steps (10 per stage): a sample of particles vs the oracle's Newton."""
+    w = synth.make_workload("batch32", count=3)
+    Bs = basis_for(32, 16)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    F = ball.expand(Bs, w.vols.astype(np.float64))
+    p = plan_for(32, 16, bh.BH_MODE_FP32)
+    q, s, sq, ss = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(F).to(dev), torch.from_numpy(w.starts).to(dev),
+                                     w.stages, 10, per_start=True, newton=True)
+    q = q.cpu().numpy().astype(np.float64)
+    fails = []
+    for b in range(w.B):
+        ref = align.align_particle(Bs, t, F[b], w.starts[b].astype(np.float64), w.stages, 10, method="newton")
+        ang = math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), ref.q))
+        srt = np.sort(ref.start_score)[::-1]
+        tied = len(srt) > 1 and (srt[0] - srt[1]) < 1e-4 * abs(srt[0])
+        if ang >= 0.1 and not tied:
+            fails.append((b, ang))
+    assert not fails, fails
