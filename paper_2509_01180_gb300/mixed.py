@@ -91,3 +91,34 @@ class MixedBatch:
     def destroy(self):
         for p in self.parts:
             p["plan"].destroy()
+
+
+def shard_classes(classes, rank: int, world: int):
+    """This rank's share of one mixed batch split over `world` GPUs: subtomograms assigned by a cost-balanced
+    partition (expansion V * Nb plus S (1 + steps) Wigner evaluations per band), classes kept, particles kept
+    in start-count order.  Returns (classes restricted to the share, per-class original indices)."""
+    import copy
+
+    from . import replicas
+    costs, owner = [], []
+    for ci, cw in enumerate(classes):
+        L = cw.Lmax
+        # basis size (FP64 roots on the host) and in-ball voxel count (centre N/2, r < 1) of the class
+        N = cw.N
+        K, _, _ = bh.bh_basis_roots(L, cw.lam_max)
+        Nb = int(sum((2 * l + 1) * int(K[l]) for l in range(L + 1)))
+        c = (np.arange(N) - N / 2) / (N / 2)
+        V = int(np.count_nonzero((c[:, None, None] ** 2 + c[None, :, None] ** 2 + c[None, None, :] ** 2) < 1.0))
+        for b in range(cw.B):
+            costs.append(replicas.particle_cost(Nb, V, int(cw.S[b]), cw.steps, cw.stages))
+            owner.append((ci, b))
+    mine = replicas.balanced_partition(costs, world)[rank]
+    out, index = [], []
+    for ci, cw in enumerate(classes):
+        sel = np.array([owner[i][1] for i in mine if owner[i][0] == ci], dtype=np.int64)
+        sub = copy.copy(cw)
+        sub.vols, sub.tmpl_index, sub.q_true = cw.vols[sel], cw.tmpl_index[sel], cw.q_true[sel]
+        sub.S, sub.starts = cw.S[sel], cw.starts[sel]
+        out.append(sub)
+        index.append(sel)
+    return out, index
