@@ -200,7 +200,8 @@ typedef struct {
                              step pi/(2L) g/|g|; d clipped to length pi/L and scaled by a damping factor
                              lam (1 at each stage start); the trial R exp(d.J) is accepted if it raises
                              the score (lam <- min(1, 2 lam)), else lam <- lam/2.  One start per thread
-                             group (starts_per_thread 0 or 1); `group` 0 picks a default */
+                             group (starts_per_thread 0 or 1); `group` may also be 32; 0 picks a
+                             default (up to a warp per start when S is small and the band large) */
 } bh_align_opts;
 
 /*
@@ -252,7 +253,8 @@ int bh_align_shifts(bh_plan* plan, const float* tmpl, const float* vols, int B, 
  * truncated at the lowest selected band).  The grid is uploaded to the current device and its
  * neighbour lists are built there: j != i is a neighbour of i when |q_i . q_j| >= cos(radius / 2)
  * (geodesic angle <= radius), the dot product summed in the order w, x, y, z in FP64.
- *   quats   host, n * 4 floats (w, x, y, z), unit quaternions; n in 1..16384; copied
+ *   quats   host, n * 4 floats (w, x, y, z), unit quaternions (|q|^2 within 1e-4 of 1, else
+ *           BH_ERR_ARG); n in 1..16384; copied
  *   radius  neighbourhood radius in radians, [0, pi]
  * The grid is owned by the caller and freed by bh_grid_destroy.  Synchronous.
  */

@@ -30,7 +30,13 @@
 // (At sin beta -> 0 the last line loses FP32 precision as eps/|sin beta|; exactly at 0 it is taken as 0.)
 //
 // Work split: one CTA per subtomogram; lane group of G threads per start; within a row m the 2m+1
-// orbits are dealt round-robin to the G lanes, which reduce their partial sums by xor-shuffles.
+// orbits are dealt round-robin to the G lanes, starting one lane earlier in every row (lane q takes the
+// orbits with n + 2m = q mod G), which balances the rows' unequal lengths across lanes (band 16: 99 %
+// of lane-steps busy at G = 4, 93 % at G = 16, against 85 % and 56 % when every row starts at lane 0).
+// A lane's first orbit in row m is n = jr - m with jr = (q - m) mod G; its phases there are
+// A^jr conj(ed)^{2m} and Bc^jr ed^{2m} (A = Es ed, Bc = Es conj(ed)), advanced from row to row by
+// conj(A) conj(ed)^2 and conj(Bc) ed^2 (times A^G, Bc^G when jr wraps).  The lanes reduce their partial
+// sums by xor-shuffles.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -147,7 +153,7 @@ template <int G, int C>
 __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
                                const float* __restrict__ lbin, Eval (&out)[C]) {
   float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
-  float2 es[C], ed[C], R1[C], R2[C], Ed2[C], Uq[C], Wrow[C];
+  float2 es[C], ed[C], R1[C], R2[C], T1[C], T2[C], P1s[C], P2s[C];
 #pragma unroll
   for (int j = 0; j < C; ++j) {
     const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
@@ -166,11 +172,16 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
     // along a lane's orbits in a row (n += G) the two phases are geometric with ratios R1, R2
     R1[j] = cmul(EsG, edG);
     R2[j] = cmul(EsG, cconj(edG));
+    // row-start phases (header comment): P1 = A^jr conj(ed)^{2m}, P2 = Bc^jr ed^{2m}
     const float2 Ed = cconj(ed[j]);
-    Ed2[j] = cmul(Ed, Ed);
-    Uq[j] = cpow(Es, qg);
-    Wrow[j] = cpow(ed[j], qg);
+    const float2 Ed2 = cmul(Ed, Ed);
+    const float2 A = cmul(Es, ed[j]), Bc = cmul(Es, Ed);
+    P1s[j] = cpow(A, qg);
+    P2s[j] = cpow(Bc, qg);
+    T1[j] = cmul(cconj(A), Ed2);
+    T2[j] = cmul(cconj(Bc), cconj(Ed2));
   }
+  int jr = qg;
   float S[C], Sa[C], Sb[C], Sg[C];
 #pragma unroll
   for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
@@ -183,11 +194,11 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
     float rS[C], rI1[C], rI2[C], rN1[C], rN2[C], rB[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      P1[j] = cmul(Uq[j], Wrow[j]);
-      P2[j] = cmul(Uq[j], cconj(Wrow[j]));
+      P1[j] = P1s[j];
+      P2[j] = P2s[j];
       rS[j] = rI1[j] = rI2[j] = rN1[j] = rN2[j] = rB[j] = 0.f;
     }
-    for (int n = qg - m; n <= m; n += G) {
+    for (int n = jr - m; n <= m; n += G) {
       const float lb = __ldg(lbin + m * kBinStride + m + n);
       const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
       const bool odd = (m - n) & 1;
@@ -263,8 +274,14 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
       Sa[j] += fm * rI1[j] + rN2[j];
       Sg[j] += rN1[j] + fm * rI2[j];
       Sb[j] += rB[j];
-      Wrow[j] = cmul(Wrow[j], Ed2[j]);
+      P1s[j] = cmul(P1s[j], T1[j]);
+      P2s[j] = cmul(P2s[j], T2[j]);
+      if (jr == 0) {
+        P1s[j] = cmul(P1s[j], R1[j]);
+        P2s[j] = cmul(P2s[j], R2[j]);
+      }
     }
+    jr = (jr == 0) ? G - 1 : jr - 1;
   }
 #pragma unroll
   for (int j = 0; j < C; ++j) {
@@ -396,19 +413,21 @@ __device__ EvalH eval_hess(const float4* __restrict__ tab, int Lb, int L, float4
   const float2 R1 = cmul(EsG, edG), R2 = cmul(EsG, cconj(edG));
   const float2 Ed = cconj(ed);
   const float2 Ed2 = cmul(Ed, Ed);
-  const float2 Uq = cpow(Es, qg);
-  float2 Wrow = cpow(ed, qg);
+  const float2 A = cmul(Es, ed), Bc = cmul(Es, Ed);
+  float2 P1s = cpow(A, qg), P2s = cpow(Bc, qg);
+  const float2 T1 = cmul(cconj(A), Ed2), T2 = cmul(cconj(Bc), cconj(Ed2));
+  int jr = qg;
   float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
   float Saa = 0.f, Sab = 0.f, Sag = 0.f, Sbg = 0.f, Sgg = 0.f, Sk = 0.f, SL = 0.f;
   for (int m = 0; m <= L; ++m) {
     const int wd = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
     const float fm2 = (float)(m * m), fm = (float)m;
-    float2 P1 = cmul(Uq, Wrow), P2 = cmul(Uq, cconj(Wrow));
+    float2 P1 = P1s, P2 = P2s;
     float rS = 0.f, rI1 = 0.f, rI2 = 0.f, rN1 = 0.f, rN2 = 0.f, rB = 0.f;
     float hU1 = 0.f, hU2 = 0.f, hUn1 = 0.f, hUn2 = 0.f, hUnn1 = 0.f, hUnn2 = 0.f;
     float hY1 = 0.f, hY2 = 0.f, hYn1 = 0.f, hYn2 = 0.f, hL = 0.f;
-    for (int n = qg - m; n <= m; n += G) {
+    for (int n = jr - m; n <= m; n += G) {
       const float lb = __ldg(lbin + m * kBinStride + m + n);
       const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
       const float4* ep = rowp + (n + m);
@@ -471,7 +490,13 @@ __device__ EvalH eval_hess(const float4* __restrict__ tab, int Lb, int L, float4
     Sbg += hYn1 + fm * hY2;
     Sk += fm2 * (hU1 + hU2) + (hUnn1 + hUnn2) - 2.f * xb * fm * (hUn1 + hUn2);
     SL += hL;
-    Wrow = cmul(Wrow, Ed2);
+    P1s = cmul(P1s, T1);
+    P2s = cmul(P2s, T2);
+    if (jr == 0) {
+      P1s = cmul(P1s, R1);
+      P2s = cmul(P2s, R2);
+    }
+    jr = (jr == 0) ? G - 1 : jr - 1;
   }
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) {
@@ -898,15 +923,18 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
   const double xb = (cb - sb) * (cb + sb);
   const double lcc = log2(fmax(cb, 1e-300)), lss = log2(fmax(sb, 1e-300));
   const Cx64 Es = cj64(es), EsG = cp64(Es, G), edG = cp64(ed, G), Ed = cj64(ed), Ed2 = cm64(Ed, Ed);
-  const Cx64 Uq = cp64(Es, qg);
-  Cx64 Wrow = cp64(ed, qg);
+  const Cx64 A = cm64(Es, ed), Bc = cm64(Es, Ed);
+  const Cx64 R1 = cm64(EsG, edG), R2 = cm64(EsG, cj64(edG));
+  const Cx64 T1 = cm64(cj64(A), Ed2), T2 = cm64(cj64(Bc), cj64(Ed2));
+  Cx64 P1s = cp64(A, qg), P2s = cp64(Bc, qg);
+  int jr = qg;
   double S = 0.0;
   for (int m = 0; m <= L; ++m) {
     const int w2 = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
     const double2* crow = coef + tab_base(m, Lmax);
-    Cx64 U = Uq, W = Wrow;
-    for (int n = qg - m; n <= m; n += G) {
+    Cx64 P1 = P1s, P2 = P2s;
+    for (int n = jr - m; n <= m; n += G) {
       double d = exp2(lbin[m * kBinStride + m + n] + (double)(m + n) * lcc + (double)(m - n) * lss);
       d = ((m - n) & 1) ? -d : d;
       const float4* ep = rowp + (n + m);
@@ -927,12 +955,17 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
         a2r = fma(en, (double)xv.z, a2r);
         a2i = fma(en, (double)xv.w, a2i);
       }
-      const Cx64 P1 = cm64(U, W), P2 = cm64(U, cj64(W));
       S += (P1.x * a1r - P1.y * a1i) + (P2.x * a2r - P2.y * a2i);
-      U = cm64(U, EsG);
-      W = cm64(W, edG);
+      P1 = cm64(P1, R1);
+      P2 = cm64(P2, R2);
     }
-    Wrow = cm64(Wrow, Ed2);
+    P1s = cm64(P1s, T1);
+    P2s = cm64(P2s, T2);
+    if (jr == 0) {
+      P1s = cm64(P1s, R1);
+      P2s = cm64(P2s, R2);
+    }
+    jr = (jr == 0) ? G - 1 : jr - 1;
   }
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
@@ -1129,7 +1162,8 @@ int launch_newton(const AlignArgs& a, int G, bool score_only, int L, cudaStream_
     case 4: return launch_newton_g<4>(a, score_only, L, stream);
     case 8: return launch_newton_g<8>(a, score_only, L, stream);
     case 16: return launch_newton_g<16>(a, score_only, L, stream);
-    default: return fail(BH_ERR_ARG, "group %d not in {1,2,4,8,16}", G);
+    case 32: return launch_newton_g<32>(a, score_only, L, stream);
+    default: return fail(BH_ERR_ARG, "group %d not in {1,2,4,8,16,32}", G);
   }
 }
 
@@ -1167,6 +1201,17 @@ int default_group(int S, int Lb) {
   const int want = std::max(32, 512 / ctas);
   int G = 1;
   while (G < 16 && S * G < want && round_up(S * G * 2, 32) <= kMaxThreads) G *= 2;
+  return G;
+}
+
+// Default lanes per start of the Newton kernel: about 256 resident threads per SM (its evaluation holds
+// more state per lane than the ascent's, measured best at one warp per CTA for band 16), up to a full
+// warp per start (few candidate starts on a large orbit table would otherwise leave an SM idle).
+int default_group_newton(int S, int Lb) {
+  const int ctas = std::max(1, std::min(8, (int)(232448 / std::max<size_t>(1, table_bytes(Lb)))));
+  const int want = std::max(32, 256 / ctas);
+  int G = 1;
+  while (G < 32 && S * G < want && round_up(S * G * 2, 32) <= kMaxThreads) G *= 2;
   return G;
 }
 
@@ -1312,7 +1357,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   if (C == 0) C = 1;
   if (opts && opts->newton) {
     if (opts->starts_per_thread > 1) return fail(BH_ERR_ARG, "Newton steps run one start per thread group");
-    if (opts->group == 0) G = default_group(S, a.Lb);
+    if (opts->group == 0) G = default_group_newton(S, a.Lb);
     if (round_up(S * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
     st = launch_newton(a, G, false, 0, static_cast<cudaStream_t>(stream));
@@ -1556,8 +1601,12 @@ namespace {
 constexpr int kGridMax = 16384;  // the sort keys of one subtomogram's grid scores live in shared memory
 constexpr int kCandThreads = 256;
 
-// |q_i . q_j| >= c, the dot product summed in the order w, x, y, z in FP64 (exact products of floats).
-__device__ __forceinline__ bool within(float4 a, float4 b, double c) {
+// |q_i . q_j| >= c, the dot product summed in the order w, x, y, z in FP64 (exact products of floats).  An
+// FP32 dot product decides every pair farther than 1e-5 from the threshold (its error is below 1e-6);
+// the rest take the FP64 sum, so the relation is exactly the FP64 one.
+__device__ __forceinline__ bool within(float4 a, float4 b, double c, float cf) {
+  const float d32 = fabsf(fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x))));
+  if (fabsf(d32 - cf) > 1e-5f) return d32 > cf;
   double d = __dmul_rn((double)a.x, (double)b.x);
   d = __dadd_rn(d, __dmul_rn((double)a.y, (double)b.y));
   d = __dadd_rn(d, __dmul_rn((double)a.z, (double)b.z));
@@ -1565,20 +1614,25 @@ __device__ __forceinline__ bool within(float4 a, float4 b, double c) {
   return fabs(d) >= c;
 }
 
-// Pass 1 (count) and pass 2 (fill, off != NULL) of the neighbour lists; one thread per grid point.
+// Pass 1 (count) and pass 2 (fill, off != NULL) of the neighbour lists; one warp per grid point, lanes
+// over j in chunks of 32, ballot compaction keeps each list ascending.
 __global__ void k_grid_nbr(const float4* __restrict__ q, int n, double c, const int* __restrict__ off,
                            int* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // uniform per warp
   const float4 qi = q[i];
+  const float cf = (float)c;
   int cnt = 0;
   int* dst = off ? out + off[i] : nullptr;
-  for (int j = 0; j < n; ++j) {
-    if (j == i || !within(qi, q[j], c)) continue;
-    if (dst) dst[cnt] = j;
-    ++cnt;
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int j = j0 + lane;
+    const bool hit = j < n && j != i && within(qi, q[j], c, cf);
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit && dst) dst[cnt + __popc(m & ((1u << lane) - 1u))] = j;
+    cnt += __popc(m);
   }
-  if (!off) out[i] = cnt;
+  if (!off && lane == 0) out[i] = cnt;
 }
 
 // Sort key of grid point i: [local-maximum flag : 1][score, order-preserving bits : 32][~i : 31], so that a
@@ -1606,7 +1660,7 @@ constexpr int kSelectRounds = 64;  // up to this many candidates: S rounds of a 
 // local-maximum flags from the neighbour lists, then the S highest keys, either by S rounds of a block-wide
 // argmax (S <= kSelectRounds) or by a bitonic sort of next_pow2(n) keys.
 template <int C>
-__global__ void __launch_bounds__(kCandThreads, 2) k_grid_candidates(const AlignArgs a, const GridArgs g) {
+__global__ void __launch_bounds__(kCandThreads, 3) k_grid_candidates(const AlignArgs a, const GridArgs g) {
   extern __shared__ float4 smem_tab[];
   __shared__ unsigned long long wbest[kCandThreads / 32];
   const int p = blockIdx.x;
@@ -1725,8 +1779,11 @@ extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double r
   if (!quats) return fail(BH_ERR_ARG, "quats is NULL");
   if (n < 1 || n > kGridMax) return fail(BH_ERR_ARG, "n=%d outside 1..%d", n, kGridMax);
   if (!(radius >= 0.0 && radius <= 3.141592653589793)) return fail(BH_ERR_ARG, "radius=%g outside [0, pi]", radius);
-  for (int i = 0; i < 4 * n; ++i)
-    if (!std::isfinite(quats[i])) return fail(BH_ERR_ARG, "grid rotation %d is not finite", i / 4);
+  for (int i = 0; i < n; ++i) {
+    const double w = quats[4 * i], x = quats[4 * i + 1], y = quats[4 * i + 2], z = quats[4 * i + 3];
+    const double r2 = w * w + x * x + y * y + z * z;
+    if (!std::isfinite(r2) || std::fabs(r2 - 1.0) > 1e-4) return fail(BH_ERR_ARG, "grid rotation %d is not a unit quaternion", i);
+  }
   std::unique_ptr<bh_grid, int (*)(bh_grid*)> g(new bh_grid(), bh_grid_destroy);
   BH_CUDA_TRY(cudaGetDevice(&g->device));
   g->n = n;
@@ -1739,7 +1796,8 @@ extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double r
   BH_CUDA_TRY(cudaMemcpy(g->d_q, quats, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice));
   int* d_cnt = nullptr;
   BH_CUDA_TRY(cudaMalloc(&d_cnt, (size_t)n * sizeof(int)));
-  k_grid_nbr<<<(n + 127) / 128, 128>>>(g->d_q, n, c, nullptr, d_cnt);
+  const unsigned nbr_blocks = (unsigned)(((size_t)n * 32 + 255) / 256);
+  k_grid_nbr<<<nbr_blocks, 256>>>(g->d_q, n, c, nullptr, d_cnt);
   std::vector<int> cnt(n), off(n + 1, 0);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), d_cnt, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost);
@@ -1752,7 +1810,7 @@ extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double r
   g->n_edges = off[n];
   BH_CUDA_TRY(cudaMemcpy(g->d_off, off.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice));
   BH_CUDA_TRY(cudaMalloc(&g->d_nbr, (size_t)std::max<long long>(1, g->n_edges) * sizeof(int)));
-  k_grid_nbr<<<(n + 127) / 128, 128>>>(g->d_q, n, c, g->d_off, g->d_nbr);
+  k_grid_nbr<<<nbr_blocks, 256>>>(g->d_q, n, c, g->d_off, g->d_nbr);
   BH_CHECK_LAUNCH();
   BH_CUDA_TRY(cudaDeviceSynchronize());
   *out = g.release();

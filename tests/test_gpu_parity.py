@@ -408,7 +408,7 @@ def test_newton_pair16_matches_oracle(dev):
     f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
     ref = align.align_particle(Bs, t, f, w.starts[0].astype(np.float64), w.stages, 15, method="newton")
     p = plan_for(16, 8, bh.BH_MODE_FP32)
-    for group in (1, 4):
+    for group in (1, 4, 32):
         q, s = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev), torch.from_numpy(w.starts).to(dev),
                                  w.stages, 15, group=group, newton=True)
         q = q.cpu().numpy()[0].astype(np.float64)
