@@ -354,6 +354,7 @@ def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
     n_grid, radius = args.sec3_grid, math.radians(args.sec3_radius)
     grid = bh.bh_grid_create(synth.super_fibonacci(n_grid), radius)
     S = args.sec3_starts
+    tune = bh.bh_autotune_newton(plan, B, S, w.stages, args.sec3_steps) if not args.no_autotune else None
     cst = torch.empty((B, S, 4), dtype=torch.float32, device=device)
     quat = torch.empty((B, 4), dtype=torch.float32, device=device)
     score = torch.empty((B,), dtype=torch.float32, device=device)
@@ -368,7 +369,7 @@ def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
         if ev:
             ev[2].record(stream)
         bh.bh_align_batch(plan, tmpl, coeffs, cst, w.stages, args.sec3_steps, quat_out=quat, score_out=score,
-                          stream=stream, newton=True)
+                          stream=stream, newton=True, refine_fp64=min(args.refine, S))
         if ev:
             ev[3].record(stream)
 
@@ -395,8 +396,9 @@ def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
             "median_angle_vs_truth_deg": float(np.median(ang)), "frac_within_2deg": float(np.mean(ang < 2.0)),
             "config": {"grid": f"super-Fibonacci {n_grid} rotations, neighbour radius {args.sec3_radius:g} deg",
                        "candidate_band": w.stages[0], "candidates": S, "newton_steps_per_band": args.sec3_steps,
-                       "bands": w.stages},
-            "gpu_launches_per_step": 5}
+                       "bands": w.stages, "fp64_rescore_top_k": min(args.refine, S),
+                       "newton_lanes_per_start": tune["newton_group"] if tune else "default"},
+            "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 2 + (1 if min(args.refine, S) else 0)}
 
 
 def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
@@ -530,7 +532,8 @@ def main():
                     help="also time the Sec. III protocol (candidates + Newton); default: on for batch32")
     ap.add_argument("--sec3-grid", type=int, default=4608, help="rotation grid size for the candidate starts")
     ap.add_argument("--sec3-radius", type=float, default=25.0, help="neighbour radius of the grid (degrees)")
-    ap.add_argument("--sec3-starts", type=int, default=4, help="candidate starts per subtomogram")
+    ap.add_argument("--sec3-starts", type=int, default=None,
+                    help="candidate starts per subtomogram (default 4 at 32^3, 8 at 64^3)")
     ap.add_argument("--sec3-steps", type=int, default=8, help="Newton steps per marching band")
     args = ap.parse_args()
 
@@ -560,7 +563,9 @@ def main():
     if args.refine is None:
         args.refine = 4 if args.workload == "precision64" else 0
     if args.sec3 is None:
-        args.sec3 = 1 if args.workload == "batch32" else 0
+        args.sec3 = 1 if args.workload in ("batch32", "precision64") else 0
+    if args.sec3_starts is None:
+        args.sec3_starts = 8 if args.workload == "precision64" else 4
     if args.workload == "mixed":
         line = run_mixed(args, device, rank, world)
         if rank == 0:
@@ -626,7 +631,7 @@ def main():
             "clocks": clocks,
             "e2e": {"value": world * B / (r["e2e_ms"] / args.steps / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
-            "gpu_launches": 4 * args.steps * max(1, math.ceil(B / min(B, 4096))),
+            "gpu_launches": args.steps * (3 * math.ceil(B / min(B, 4096)) + 1 + (1 if args.refine else 0)),
         }
         qt_inv = w.q_true * np.array([1, -1, -1, -1])
         acc = {"median_angle_vs_truth_deg": float(np.median(angle_deg(r["q"], qt_inv)))}

@@ -305,6 +305,14 @@ typedef struct {
  */
 int bh_autotune(bh_plan* plan, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out);
 
+/*
+ * Time the Newton kernel (opts.newton) with 1, 2, 4, 8, 16 and 32 lanes per start for this shape and keep
+ * the fastest in the plan for (band stages[nstages-1], S); bh_align_batch with opts.newton and group 0
+ * uses it.  out (may be NULL) receives align_group and align_ms; the other fields are zero.  Synchronous;
+ * allocates and frees its own scratch.
+ */
+int bh_autotune_newton(bh_plan* plan, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out);
+
 /* ------------------------------------------------------------------ random starts */
 /*
  * Uniform random rotations for the multi-start ascent (the paper starts from local maxima of the

@@ -23,7 +23,7 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
            "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_grid_create", "bh_grid_destroy", "bh_grid_info",
-           "bh_grid_neighbors", "bh_candidates", "bh_energy", "bh_autotune", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_grid_neighbors", "bh_candidates", "bh_energy", "bh_autotune", "bh_autotune_newton", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
@@ -355,6 +355,15 @@ def bh_autotune(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
     return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
 
+def bh_autotune_newton(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
+    """Time the Newton kernel's lanes per start for this shape and keep the fastest in the plan."""
+    st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
+    r = TuneResult()
+    _check(lib().bh_autotune_newton(plan.handle, B, S, st, len(stages), steps, ctypes.byref(r)),
+           "bh_autotune_newton")
+    return {"newton_group": r.align_group, "newton_ms": r.align_ms}
+
+
 class ServeOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int)]
@@ -377,6 +386,7 @@ def _serve_sigs(L):
         return
     L.bh_random_starts.argtypes = [ctypes.c_uint64, i, i, vp]
     L.bh_autotune.argtypes = [vp, i, i, vp, i, i, ctypes.POINTER(TuneResult)]
+    L.bh_autotune_newton.argtypes = [vp, i, i, vp, i, i, ctypes.POINTER(TuneResult)]
     L.bh_energy.argtypes = [vp, vp, vp, i, i, vp, i, vp, vp]
     L.bh_align_shifts_workspace.argtypes = [vp, i, i, i]
     L.bh_align_shifts_workspace.restype = ctypes.c_size_t

@@ -1357,7 +1357,10 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   if (C == 0) C = 1;
   if (opts && opts->newton) {
     if (opts->starts_per_thread > 1) return fail(BH_ERR_ARG, "Newton steps run one start per thread group");
-    if (opts->group == 0) G = default_group_newton(S, a.Lb);
+    if (opts->group == 0) {
+      auto it = p->newton_group.find({a.Lb, S});
+      G = it != p->newton_group.end() ? it->second : default_group_newton(S, a.Lb);
+    }
     if (round_up(S * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
     st = launch_newton(a, G, false, 0, static_cast<cudaStream_t>(stream));
@@ -1480,6 +1483,79 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
     out->align_ms = best_ms;
     out->gemm_bn = best_bn;
     out->expand_ms = best_ems;
+  }
+  return BH_OK;
+}
+
+extern "C" int bh_autotune_newton(bh_plan* p, int B, int S, const int* stages, int nstages, int steps,
+                                  bh_tune_result* out) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 1 || B > (1 << 20)) return fail(BH_ERR_ARG, "B=%d", B);
+  if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d", S);
+  if (!stages || nstages < 1 || nstages > kMaxStages) return fail(BH_ERR_ARG, "nstages=%d", nstages);
+  const int Lb = stages[nstages - 1];
+  if (Lb < 1 || Lb > p->Lmax) return fail(BH_ERR_ARG, "band %d", Lb);
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float *coef = nullptr, *tmpl = nullptr, *starts = nullptr, *quat = nullptr, *score = nullptr;
+  auto cleanup = [&]() {
+    if (st) cudaStreamSynchronize(st);
+    cudaFree(coef); cudaFree(tmpl); cudaFree(starts); cudaFree(quat); cudaFree(score);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+  };
+  auto cuda_fail = [&](cudaError_t e, const char* what) {
+    cleanup();
+    return fail(e == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  };
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMalloc(&coef, (size_t)B * p->Nb * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&tmpl, (size_t)p->Nb * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&starts, (size_t)B * S * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&quat, (size_t)B * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&score, (size_t)B * 4);
+  // every iteration evaluates its trial rotation whatever the data, so constant bytes time it faithfully
+  if (e == cudaSuccess) e = cudaMemsetAsync(coef, 0x3C, (size_t)B * p->Nb * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tmpl, 0x3C, (size_t)p->Nb * 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(starts, 0x3C, (size_t)B * S * 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune setup");
+  int best_g = 0;
+  float best_ms = 1e30f;
+  for (int G : {1, 2, 4, 8, 16, 32}) {
+    if (round_up(S * G, 32) > kMaxThreads) continue;
+    bh_align_opts o{};
+    o.group = G;
+    o.newton = 1;
+    int rc = BH_OK;
+    for (int it = 0; it < 2 && rc == BH_OK; ++it)
+      rc = bh_align_batch(p, tmpl, coef, B, starts, S, stages, nstages, steps, quat, score, &o, st);
+    if (rc != BH_OK) continue;
+    e = cudaEventRecord(e0, st);
+    for (int it = 0; it < 3 && e == cudaSuccess; ++it)
+      bh_align_batch(p, tmpl, coef, B, starts, S, stages, nstages, steps, quat, score, &o, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    ms /= 3.f;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_g = G;
+    }
+  }
+  cleanup();
+  if (best_g == 0) return fail(BH_ERR_UNSUPPORTED, "no Newton variant runs for S=%d band %d", S, Lb);
+  p->newton_group[{Lb, S}] = best_g;
+  if (out) {
+    *out = bh_tune_result{};
+    out->align_group = best_g;
+    out->align_starts_per_thread = 1;
+    out->align_ms = best_ms;
   }
   return BH_OK;
 }

@@ -83,6 +83,7 @@ struct bh_plan {
   int ksplit_max = 1;               // K splits the GEMM-output scratch holds
   CUtensorMap tm_xhi, tm_xlo, tm_thi, tm_tlo;  // TMA descriptors (BF16 mode)
   std::map<std::pair<int, int>, std::pair<int, int>> align_group;  // autotuned (lanes, starts per thread) by (band, S)
+  std::map<std::pair<int, int>, int> newton_group;                 // autotuned lanes per start of the Newton kernel
 };
 
 namespace bh {

@@ -434,6 +434,22 @@ def test_newton_exact_rotation_converges(dev):
         assert math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), wigner.quat_conj(qs[b]))) < 0.02
 
 
+def test_newton_autotune_picks_a_group_and_results_stay_correct(dev):
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    p = bh.bh_plan_create(16, 8, math.pi * 8, bh.BH_MODE_FP32)
+    r = bh.bh_autotune_newton(p, 64, w.S, w.stages, 15)
+    assert r["newton_group"] in (1, 2, 4, 8, 16, 32) and r["newton_ms"] > 0
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = align.align_particle(Bs, t, f, w.starts[0].astype(np.float64), w.stages, 15, method="newton")
+    q, _ = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev), torch.from_numpy(w.starts).to(dev),
+                             w.stages, 15, newton=True)
+    q = q.cpu().numpy()[0].astype(np.float64)
+    assert math.degrees(wigner.geodesic_angle(q / np.linalg.norm(q), ref.q)) < 0.1
+    p.destroy()
+
+
 @pytest.mark.slow
 def test_newton_batch32_sample(dev):
     """1024 x 32^3 workload shape with Newton steps (10 per stage): a sample of particles vs the oracle's Newton."""
