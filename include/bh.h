@@ -8,7 +8,9 @@
  *      psi_klm = c_lk j_l(lambda_lk r) Y_l^m(theta, phi) chi_[0,1)(r)   (Sec. II-A), and
  *   2. maximisation over rotations g of the rotational cross-correlation of Eq. 2 at shift s = 0,
  *      C(g) = sum_{l<=L} sum_{m,m'} xi_{l,m,m'} D^l_{m,m'}(g), with its closed-form gradient,
- *      multi-start gradient ascent and frequency marching (Sec. II-C).
+ *      multi-start gradient ascent and frequency marching (Sec. II-C); the closed-form Hessian and
+ *      damped Newton steps, and candidate starts from the local maxima of the lowest band on a
+ *      rotation grid (Sec. III); and the search over a grid of integer shifts (Eq. 1).
  *
  * Conventions (all calls):
  *   - Every call returns an int status: BH_OK (0), BH_PENDING (1, serving poll only) or a
@@ -16,7 +18,8 @@
  *     failure on the calling thread.
  *   - Array arguments documented as "device" are device pointers owned by the caller (for
  *     example allocated by PyTorch); the library never frees them.  "host" arrays are ordinary
- *     host memory.  Handles (bh_plan, bh_server) are created and destroyed by the library.
+ *     host memory.  Handles (bh_plan, bh_grid, bh_server) are created and destroyed by the
+ *     library.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Device work is
  *     enqueued asynchronously on it; the call returns once the work is queued.  Argument errors
  *     are reported before anything is enqueued.

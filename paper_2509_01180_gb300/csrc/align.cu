@@ -30,13 +30,9 @@
 // (At sin beta -> 0 the last line loses FP32 precision as eps/|sin beta|; exactly at 0 it is taken as 0.)
 //
 // Work split: one CTA per subtomogram; lane group of G threads per start; within a row m the 2m+1
-// orbits are dealt round-robin to the G lanes, starting one lane earlier in every row (lane q takes the
-// orbits with n + 2m = q mod G), which balances the rows' unequal lengths across lanes (band 16: 99 %
-// of lane-steps busy at G = 4, 93 % at G = 16, against 85 % and 56 % when every row starts at lane 0).
-// A lane's first orbit in row m is n = jr - m with jr = (q - m) mod G; its phases there are
-// A^jr conj(ed)^{2m} and Bc^jr ed^{2m} (A = Es ed, Bc = Es conj(ed)), advanced from row to row by
-// conj(A) conj(ed)^2 and conj(Bc) ed^2 (times A^G, Bc^G when jr wraps).  The lanes reduce their partial
-// sums by xor-shuffles.
+// orbits are dealt round-robin to the G lanes, which reduce their partial sums by xor-shuffles.  (The
+// lanes of a warp step through the rows in lockstep, so a row costs the warp its longest lane whatever
+// the dealing; only the FP64 re-score, whose starts span several warps, deals by flat orbit index.)
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -153,7 +149,7 @@ template <int G, int C>
 __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
                                const float* __restrict__ lbin, Eval (&out)[C]) {
   float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
-  float2 es[C], ed[C], R1[C], R2[C], T1[C], T2[C], P1s[C], P2s[C];
+  float2 es[C], ed[C], R1[C], R2[C], Ed2[C], Uq[C], Wrow[C];
 #pragma unroll
   for (int j = 0; j < C; ++j) {
     const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
@@ -172,16 +168,11 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
     // along a lane's orbits in a row (n += G) the two phases are geometric with ratios R1, R2
     R1[j] = cmul(EsG, edG);
     R2[j] = cmul(EsG, cconj(edG));
-    // row-start phases (header comment): P1 = A^jr conj(ed)^{2m}, P2 = Bc^jr ed^{2m}
     const float2 Ed = cconj(ed[j]);
-    const float2 Ed2 = cmul(Ed, Ed);
-    const float2 A = cmul(Es, ed[j]), Bc = cmul(Es, Ed);
-    P1s[j] = cpow(A, qg);
-    P2s[j] = cpow(Bc, qg);
-    T1[j] = cmul(cconj(A), Ed2);
-    T2[j] = cmul(cconj(Bc), cconj(Ed2));
+    Ed2[j] = cmul(Ed, Ed);
+    Uq[j] = cpow(Es, qg);
+    Wrow[j] = cpow(ed[j], qg);
   }
-  int jr = qg;
   float S[C], Sa[C], Sb[C], Sg[C];
 #pragma unroll
   for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
@@ -194,11 +185,11 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
     float rS[C], rI1[C], rI2[C], rN1[C], rN2[C], rB[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      P1[j] = P1s[j];
-      P2[j] = P2s[j];
+      P1[j] = cmul(Uq[j], Wrow[j]);
+      P2[j] = cmul(Uq[j], cconj(Wrow[j]));
       rS[j] = rI1[j] = rI2[j] = rN1[j] = rN2[j] = rB[j] = 0.f;
     }
-    for (int n = jr - m; n <= m; n += G) {
+    for (int n = qg - m; n <= m; n += G) {
       const float lb = __ldg(lbin + m * kBinStride + m + n);
       const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
       const bool odd = (m - n) & 1;
@@ -274,14 +265,8 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
       Sa[j] += fm * rI1[j] + rN2[j];
       Sg[j] += rN1[j] + fm * rI2[j];
       Sb[j] += rB[j];
-      P1s[j] = cmul(P1s[j], T1[j]);
-      P2s[j] = cmul(P2s[j], T2[j]);
-      if (jr == 0) {
-        P1s[j] = cmul(P1s[j], R1[j]);
-        P2s[j] = cmul(P2s[j], R2[j]);
-      }
+      Wrow[j] = cmul(Wrow[j], Ed2[j]);
     }
-    jr = (jr == 0) ? G - 1 : jr - 1;
   }
 #pragma unroll
   for (int j = 0; j < C; ++j) {
@@ -413,21 +398,19 @@ __device__ EvalH eval_hess(const float4* __restrict__ tab, int Lb, int L, float4
   const float2 R1 = cmul(EsG, edG), R2 = cmul(EsG, cconj(edG));
   const float2 Ed = cconj(ed);
   const float2 Ed2 = cmul(Ed, Ed);
-  const float2 A = cmul(Es, ed), Bc = cmul(Es, Ed);
-  float2 P1s = cpow(A, qg), P2s = cpow(Bc, qg);
-  const float2 T1 = cmul(cconj(A), Ed2), T2 = cmul(cconj(Bc), cconj(Ed2));
-  int jr = qg;
+  const float2 Uq = cpow(Es, qg);
+  float2 Wrow = cpow(ed, qg);
   float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
   float Saa = 0.f, Sab = 0.f, Sag = 0.f, Sbg = 0.f, Sgg = 0.f, Sk = 0.f, SL = 0.f;
   for (int m = 0; m <= L; ++m) {
     const int wd = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
     const float fm2 = (float)(m * m), fm = (float)m;
-    float2 P1 = P1s, P2 = P2s;
+    float2 P1 = cmul(Uq, Wrow), P2 = cmul(Uq, cconj(Wrow));
     float rS = 0.f, rI1 = 0.f, rI2 = 0.f, rN1 = 0.f, rN2 = 0.f, rB = 0.f;
     float hU1 = 0.f, hU2 = 0.f, hUn1 = 0.f, hUn2 = 0.f, hUnn1 = 0.f, hUnn2 = 0.f;
     float hY1 = 0.f, hY2 = 0.f, hYn1 = 0.f, hYn2 = 0.f, hL = 0.f;
-    for (int n = jr - m; n <= m; n += G) {
+    for (int n = qg - m; n <= m; n += G) {
       const float lb = __ldg(lbin + m * kBinStride + m + n);
       const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
       const float4* ep = rowp + (n + m);
@@ -490,13 +473,7 @@ __device__ EvalH eval_hess(const float4* __restrict__ tab, int Lb, int L, float4
     Sbg += hYn1 + fm * hY2;
     Sk += fm2 * (hU1 + hU2) + (hUnn1 + hUnn2) - 2.f * xb * fm * (hUn1 + hUn2);
     SL += hL;
-    P1s = cmul(P1s, T1);
-    P2s = cmul(P2s, T2);
-    if (jr == 0) {
-      P1s = cmul(P1s, R1);
-      P2s = cmul(P2s, R2);
-    }
-    jr = (jr == 0) ? G - 1 : jr - 1;
+    Wrow = cmul(Wrow, Ed2);
   }
 #pragma unroll
   for (int o = 1; o < G; o <<= 1) {
@@ -911,31 +888,58 @@ __device__ __forceinline__ Cx64 cp64(Cx64 a, int k) {
   return r;
 }
 
-template <int G>
-__device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L, float4 qf, int qg,
-                                   const double2* __restrict__ coef, const double* __restrict__ lbin, int Lmax) {
+__device__ __forceinline__ Cx64 cpow64(Cx64 a, int k) {  // a^k, k >= 0, by binary exponentiation
+  Cx64 r{1.0, 0.0};
+  while (k > 0) {
+    if (k & 1) r = cm64(r, a);
+    a = cm64(a, a);
+    k >>= 1;
+  }
+  return r;
+}
+
+// Half-angle phases of a rotation (FP64): es = e^{i(alpha+gamma)/2}, ed = e^{i(alpha-gamma)/2}.
+struct Rot64 {
+  Cx64 es, ed;
+  double xb, lcc, lss;
+};
+__device__ __forceinline__ Rot64 rot64(float4 qf) {
   double w = qf.x, x = qf.y, y = qf.z, z = qf.w;
   const double nq = 1.0 / sqrt(w * w + x * x + y * y + z * z);
   w *= nq; x *= nq; y *= nq; z *= nq;
   const double cb = sqrt(w * w + z * z), sb = sqrt(x * x + y * y);
-  const Cx64 es = cb > 0.0 ? Cx64{w / cb, z / cb} : Cx64{1.0, 0.0};
-  const Cx64 ed = sb > 0.0 ? Cx64{y / sb, -x / sb} : Cx64{1.0, 0.0};
-  const double xb = (cb - sb) * (cb + sb);
-  const double lcc = log2(fmax(cb, 1e-300)), lss = log2(fmax(sb, 1e-300));
-  const Cx64 Es = cj64(es), EsG = cp64(Es, G), edG = cp64(ed, G), Ed = cj64(ed), Ed2 = cm64(Ed, Ed);
-  const Cx64 A = cm64(Es, ed), Bc = cm64(Es, Ed);
-  const Cx64 R1 = cm64(EsG, edG), R2 = cm64(EsG, cj64(edG));
-  const Cx64 T1 = cm64(cj64(A), Ed2), T2 = cm64(cj64(Bc), cj64(Ed2));
-  Cx64 P1s = cp64(A, qg), P2s = cp64(Bc, qg);
-  int jr = qg;
+  Rot64 r;
+  r.es = cb > 0.0 ? Cx64{w / cb, z / cb} : Cx64{1.0, 0.0};
+  r.ed = sb > 0.0 ? Cx64{y / sb, -x / sb} : Cx64{1.0, 0.0};
+  r.xb = (cb - sb) * (cb + sb);
+  r.lcc = log2(fmax(cb, 1e-300));
+  r.lss = log2(fmax(sb, 1e-300));
+  return r;
+}
+
+// FP64 score of one rotation at band L, NL lanes per rotation (NL > 32: several warps; the caller adds the
+// per-warp partial sums).  Orbits are dealt by their flat index: lane q takes (m, n) with
+// m^2 + m + n = q mod NL, so rows shorter than NL still spread over all lanes.  The lane's first orbit in
+// row m is n = j - m, j = (q - m^2) mod NL, with phases A^j conj(ed)^{2m} and Bc^j ed^{2m}; A^j and Bc^j
+// (j < NL) come from per-rotation power tables in shared memory.  Returns the warp's partial sum.
+template <int NL>
+__device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L, const Rot64& r, int q,
+                                   const double2* __restrict__ Apow, const double2* __restrict__ Bpow,
+                                   const double2* __restrict__ coef, const double* __restrict__ lbin, int Lmax) {
+  const Cx64 Es = cj64(r.es), Ed = cj64(r.ed), Ed2 = cm64(Ed, Ed);
+  const Cx64 R1 = cpow64(cm64(Es, r.ed), NL), R2 = cpow64(cm64(Es, Ed), NL);
+  Cx64 Cm{1.0, 0.0};
   double S = 0.0;
   for (int m = 0; m <= L; ++m) {
     const int w2 = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
     const double2* crow = coef + tab_base(m, Lmax);
-    Cx64 P1 = P1s, P2 = P2s;
-    for (int n = jr - m; n <= m; n += G) {
-      double d = exp2(lbin[m * kBinStride + m + n] + (double)(m + n) * lcc + (double)(m - n) * lss);
+    int j = (q - m * m) % NL;
+    j += j < 0 ? NL : 0;
+    const double2 ap = Apow[j], bp = Bpow[j];
+    Cx64 P1 = cm64(Cx64{ap.x, ap.y}, Cm), P2 = cm64(Cx64{bp.x, bp.y}, cj64(Cm));
+    for (int n = j - m; n <= m; n += NL) {
+      double d = exp2(lbin[m * kBinStride + m + n] + (double)(m + n) * r.lcc + (double)(m - n) * r.lss);
       d = ((m - n) & 1) ? -d : d;
       const float4* ep = rowp + (n + m);
       const double2* kp = crow + (n + m);
@@ -946,7 +950,7 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
         ep += w2;
         kp += w2;
         const double2 k = __ldg(kp);
-        const double en = fma(xb - k.x, e1, -k.y * e2);
+        const double en = fma(r.xb - k.x, e1, -k.y * e2);
         e2 = e1;
         e1 = en;
         xv = *ep;
@@ -959,30 +963,31 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
       P1 = cm64(P1, R1);
       P2 = cm64(P2, R2);
     }
-    P1s = cm64(P1s, T1);
-    P2s = cm64(P2s, T2);
-    if (jr == 0) {
-      P1s = cm64(P1s, R1);
-      P2s = cm64(P2s, R2);
-    }
-    jr = (jr == 0) ? G - 1 : jr - 1;
+    Cm = cm64(Cm, Ed2);
   }
 #pragma unroll
-  for (int o = 1; o < G; o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+  for (int o = 1; o < (NL < 32 ? NL : 32); o <<= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
   return S;
 }
 
+// Top-K re-scoring in FP64 at the last band (optional): the K starts with the largest FP32 final score
+// (ties: lowest index) are re-evaluated with the d-recursion, seeds, phases and sums in FP64 (the table's
+// xi stays the FP32 product; the rational recursion coefficients come from the plan's FP64 table), and
+// the subtomogram's result is the best of them on the FP64 score.  One CTA of K * NL threads per
+// subtomogram; shared memory: the orbit table, then the per-start power tables A^j, Bc^j (j < NL).
 constexpr int kMaxRefine = 64;
 
-// Re-score the K best starts (by their FP32 final score) of every subtomogram in FP64 at band L and
-// select among them on the FP64 score (exact ties: lowest start index).  blockDim = roundup(K G, 32).
-template <int G>
+template <int NL>
 __global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, int K, const double2* coef64,
                                                      const double* lbin64) {
   extern __shared__ float4 smem_tab[];
   __shared__ int top[kMaxRefine];
-  __shared__ double s64[kMaxRefine];
+  __shared__ double part[kMaxRefine];  // [start][warp of the start] partial sums; K * max(1, NL/32) <= 64
+  constexpr int W = NL > 32 ? NL / 32 : 1;
   const int p = blockIdx.x;
+  const int ntab = tab_base(a.Lb + 1, a.Lb);
+  double2* Apow = reinterpret_cast<double2*>(smem_tab + ntab);
+  double2* Bpow = Apow + (size_t)K * NL;
   build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
               blockDim.x);
   if (threadIdx.x == 0) {
@@ -998,20 +1003,35 @@ __global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, i
     }
   }
   __syncthreads();
-  const int s = threadIdx.x / G, qg = threadIdx.x % G;
+  const int s = threadIdx.x / NL, q = threadIdx.x % NL;
   const bool active = s < K;
-  const int idx = top[active ? s : s % K];
-  const float4 q = a.start_quat_out[(size_t)p * a.S + idx];
-  const double S = score_rotation64<G>(smem_tab, a.Lb, L, q, qg, coef64, lbin64, a.lay.Lmax);
-  if (active && qg == 0) s64[s] = S;
+  const int se = active ? s : s % K;  // lanes past the last start shadow a real one and write nothing
+  const Rot64 r = rot64(a.start_quat_out[(size_t)p * a.S + top[se]]);
+  if (active) {
+    const Cx64 Es = cj64(r.es);
+    const Cx64 Ap = cpow64(cm64(Es, r.ed), q), Bp = cpow64(cm64(Es, cj64(r.ed)), q);
+    Apow[(size_t)s * NL + q] = make_double2(Ap.x, Ap.y);
+    Bpow[(size_t)s * NL + q] = make_double2(Bp.x, Bp.y);
+  }
+  __syncthreads();
+  const double S = score_rotation64<NL>(smem_tab, a.Lb, L, r, q, Apow + (size_t)se * NL, Bpow + (size_t)se * NL,
+                                        coef64, lbin64, a.lay.Lmax);
+  if (active && (q & 31) == 0) part[s * W + q / 32] = S;
   __syncthreads();
   if (threadIdx.x == 0) {
     int best = 0;
-    for (int k = 1; k < K; ++k)
-      if (s64[k] > s64[best] || (s64[k] == s64[best] && top[k] < top[best])) best = k;
+    double sbest = 0.0;
+    for (int k = 0; k < K; ++k) {
+      double sk = 0.0;
+      for (int w = 0; w < W; ++w) sk += part[k * W + w];
+      if (k == 0 || sk > sbest || (sk == sbest && top[k] < top[best])) {
+        best = k;
+        sbest = sk;
+      }
+    }
     a.quat_out[p] = a.start_quat_out[(size_t)p * a.S + top[best]];
-    a.score_out[p] = (float)s64[best];
-    if (a.score64_out) a.score64_out[p] = s64[best];
+    a.score_out[p] = (float)sbest;
+    if (a.score64_out) a.score64_out[p] = sbest;
   }
 }
 
@@ -1167,30 +1187,33 @@ int launch_newton(const AlignArgs& a, int G, bool score_only, int L, cudaStream_
   }
 }
 
-template <int G>
-int launch_refine_g(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
-  const int threads = round_up(K * G, 32);
-  const size_t smem = table_bytes(a.Lb);
+template <int NL>
+int launch_refine_nl(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
+  const int threads = round_up(K * NL, 32);
+  const size_t smem = table_bytes(a.Lb) + 2 * (size_t)K * NL * sizeof(double2);
+  if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "FP64 re-score for band %d needs %zu B of shared memory", a.Lb, smem);
   static std::atomic<int> have{0};
-  int st = ensure_smem(k_refine64<G>, have, smem);
+  int st = ensure_smem(k_refine64<NL>, have, smem);
   if (st != BH_OK) return st;
-  k_refine64<G><<<a.B, threads, smem, stream>>>(a, L, K, p->d_coef64, p->d_lbin64);
+  k_refine64<NL><<<a.B, threads, smem, stream>>>(a, L, K, p->d_coef64, p->d_lbin64);
   BH_CHECK_LAUNCH();
   return BH_OK;
 }
 
-// FP64 work needs many warps in flight; one CTA per subtomogram holds K re-scored starts with up to a full
-// warp of lanes each (at least 128 threads when K allows).
+// FP64 work needs many warps in flight (GB300's FP64 pipe is narrow and deep): one CTA per subtomogram
+// holds the K re-scored starts with up to 128 lanes (four warps) each, 512 threads when K allows.
 int launch_refine(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream_t stream) {
-  int G = 1;
-  while (G < 32 && K * G < 256 && K * G * 2 <= kMaxThreads) G *= 2;
-  switch (G) {
-    case 1: return launch_refine_g<1>(a, L, K, p, stream);
-    case 2: return launch_refine_g<2>(a, L, K, p, stream);
-    case 4: return launch_refine_g<4>(a, L, K, p, stream);
-    case 8: return launch_refine_g<8>(a, L, K, p, stream);
-    case 16: return launch_refine_g<16>(a, L, K, p, stream);
-    default: return launch_refine_g<32>(a, L, K, p, stream);
+  int NL = 1;
+  while (NL < 128 && K * NL * 2 <= kMaxThreads) NL *= 2;
+  switch (NL) {
+    case 1: return launch_refine_nl<1>(a, L, K, p, stream);
+    case 2: return launch_refine_nl<2>(a, L, K, p, stream);
+    case 4: return launch_refine_nl<4>(a, L, K, p, stream);
+    case 8: return launch_refine_nl<8>(a, L, K, p, stream);
+    case 16: return launch_refine_nl<16>(a, L, K, p, stream);
+    case 32: return launch_refine_nl<32>(a, L, K, p, stream);
+    case 64: return launch_refine_nl<64>(a, L, K, p, stream);
+    default: return launch_refine_nl<128>(a, L, K, p, stream);
   }
 }
 
