@@ -117,13 +117,43 @@ __device__ void build_table(float4* __restrict__ tab, const Layout& lay, const f
     const int l = m + rem / w, n = rem % w - m;
     const int K = lay.K[l], off = lay.off[l], wl = 2 * l + 1;
     const bool two = (m > 0) && (n != m) && (n != -m);
+    // four radial indices per iteration, so that eight (sixteen) L2 loads are in flight per thread: at
+    // large bands few warps share an SM and the build is bound by load latency
     float2 x1 = make_float2(0.f, 0.f), x2 = make_float2(0.f, 0.f);
-    for (int k = 0; k < K; ++k) {
-      const float2 tm = __ldg(tmpl + off + k * wl + m + l), fn = __ldg(sub + off + k * wl + n + l);
+    const float2* tp = tmpl + off + l;
+    const float2* fp = sub + off + l;
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+      float2 tm[4], fn[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        tm[u] = __ldg(tp + (k + u) * wl + m);
+        fn[u] = __ldg(fp + (k + u) * wl + n);
+      }
+      float2 tn[4], fm[4];
+      if (two) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          tn[u] = __ldg(tp + (k + u) * wl + n);
+          fm[u] = __ldg(fp + (k + u) * wl + m);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x1.x += tm[u].x * fn[u].x + tm[u].y * fn[u].y;
+        x1.y += tm[u].x * fn[u].y - tm[u].y * fn[u].x;
+        if (two) {
+          x2.x += tn[u].x * fm[u].x + tn[u].y * fm[u].y;
+          x2.y += tn[u].x * fm[u].y - tn[u].y * fm[u].x;
+        }
+      }
+    }
+    for (; k < K; ++k) {
+      const float2 tm = __ldg(tp + k * wl + m), fn = __ldg(fp + k * wl + n);
       x1.x += tm.x * fn.x + tm.y * fn.y;
       x1.y += tm.x * fn.y - tm.y * fn.x;
       if (two) {
-        const float2 tn = __ldg(tmpl + off + k * wl + n + l), fm = __ldg(sub + off + k * wl + m + l);
+        const float2 tn = __ldg(tp + k * wl + n), fm = __ldg(fp + k * wl + m);
         x2.x += tn.x * fm.x + tn.y * fm.y;
         x2.y += tn.x * fm.y - tn.y * fm.x;
       }
