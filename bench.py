@@ -334,7 +334,9 @@ def run_ours(args, rank, world, device):
         e2e_ms = replicas.max_over_ranks([t_first.elapsed_time(t_last)], device)[0]
         sec3 = sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) if (
             name == "bf16split" and args.sec3) else None
-        results[name] = {"sec3": sec3, "plan_s": plan_s, "tune": tune, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
+        wedge_res = wedge_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) if (
+            name == "bf16split" and args.wedge_leg) else None
+        results[name] = {"wedge": wedge_res, "sec3": sec3, "plan_s": plan_s, "tune": tune, "t_tot": t_tot, "t_exp": t_exp, "t_aln": t_aln, "q": q_res,
                          "clocks": clk.summary(), "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V,
                          "h2d": int(hv.numel() * 4), "d2h": int(hq[0].numel() * 4 + hs[0].numel() * 4)}
         plan.destroy()
@@ -399,6 +401,57 @@ def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
                        "bands": w.stages, "fp64_rescore_top_k": min(args.refine, S),
                        "newton_lanes_per_start": tune["newton_group"] if tune else "default"},
             "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 2 + (1 if min(args.refine, S) else 0)}
+
+
+def wedge_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
+    """Missing-wedge constrained correlation (Sec. II-B) on the same batch: expansion + the constrained
+    ascent (same starts, bands and steps as the main leg) with the data's own tilt half-angle."""
+    import numpy as np
+    import torch
+
+    from paper_2509_01180_gb300 import bh, replicas
+    B = w.B
+    t0 = time.perf_counter()
+    wd = bh.bh_wedge_create(plan, w.template, float(w.meta["wedge_deg"]), w.stages[-1])
+    prep_s = time.perf_counter() - t0
+    starts = torch.from_numpy(w.starts).to(device)
+    quat = torch.empty((B, 4), dtype=torch.float32, device=device)
+    score = torch.empty((B,), dtype=torch.float32, device=device)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        bh.bh_expand(plan, vols, coeffs, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
+                          stream=stream, wedge=wd)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    steps = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    torch.cuda.synchronize(device)
+    replicas.barrier()
+    for k in range(steps):
+        step(evs[k])
+        flush.zero_()
+    torch.cuda.synchronize(device)
+    replicas.barrier()
+    t = [sum(e[i].elapsed_time(e[i + 1]) for e in evs) for i in range(2)]
+    t = replicas.max_over_ranks(t, device)
+    q = quat.cpu().numpy().astype(np.float64)
+    ang = angle_deg(q, w.q_true * np.array([1, -1, -1, -1]))
+    wd.destroy()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return {"q": q, "value": world * B / (sum(t) / steps / 1e3), "unit": UNIT, "ms_per_step": sum(t) / steps,
+            "breakdown_ms_per_step": {"expand": t[0] / steps, "constrained_align": t[1] / steps},
+            "median_angle_vs_truth_deg": float(np.median(ang)), "frac_within_2deg": float(np.mean(ang < 2.0)),
+            "config": {"wedge_half_angle_deg": float(w.meta["wedge_deg"]), "norm_band": w.stages[-1],
+                       "norm_prepare_s": prep_s, "starts": w.S, "steps": w.steps, "bands": w.stages},
+            "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 1}
 
 
 def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
@@ -530,6 +583,8 @@ def main():
     ap.add_argument("--refine", type=int, default=None, help="FP64 re-scoring of the K best starts (precision form)")
     ap.add_argument("--sec3", type=int, default=None,
                     help="also time the Sec. III protocol (candidates + Newton); default: on for batch32")
+    ap.add_argument("--wedge-leg", type=int, default=None,
+                    help="also time the missing-wedge constrained correlation; default: on for batch32")
     ap.add_argument("--sec3-grid", type=int, default=4608, help="rotation grid size for the candidate starts")
     ap.add_argument("--sec3-radius", type=float, default=25.0, help="neighbour radius of the grid (degrees)")
     ap.add_argument("--sec3-starts", type=int, default=None,
@@ -564,6 +619,8 @@ def main():
         args.refine = 4 if args.workload == "precision64" else 0
     if args.sec3 is None:
         args.sec3 = 1 if args.workload in ("batch32", "precision64") else 0
+    if args.wedge_leg is None:
+        args.wedge_leg = 1 if args.workload == "batch32" else 0
     if args.sec3_starts is None:
         args.sec3_starts = 8 if args.workload == "precision64" else 4
     if args.workload == "mixed":
@@ -644,6 +701,12 @@ def main():
                                                             "align": f["t_aln"] / args.steps},
                                   "median_angle_vs_truth_deg": float(np.median(angle_deg(f["q"], qt_inv)))}
         line["accuracy"] = acc
+        if r.get("wedge"):
+            wl = dict(r["wedge"])
+            qw = wl.pop("q")
+            if "fp32" in res:
+                wl["median_angle_vs_fp32_deg"] = float(np.median(angle_deg(qw, res["fp32"]["q"])))
+            line["wedge_constrained"] = wl
         if r.get("sec3"):
             sec3 = dict(r["sec3"])
             q3 = sec3.pop("q")

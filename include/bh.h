@@ -205,6 +205,10 @@ typedef struct {
                              the score (lam <- min(1, 2 lam)), else lam <- lam/2.  One start per thread
                              group (starts_per_thread 0 or 1); `group` may also be 32; 0 picks a
                              default (up to a warp per start when S is small and the band large) */
+  const struct bh_wedge* wedge; /* NULL, or the missing-wedge norm from bh_wedge_create: maximise the
+                             constrained score C(R) = S(R) / sqrt(Dn(R)) (Sec. II-B) with the
+                             ascent's step rule and marching instead of S(R); one template (no
+                             tmpl_index), newton 0, starts_per_thread 0 or 1; score_out then holds C */
 } bh_align_opts;
 
 /*
@@ -289,6 +293,31 @@ int bh_grid_neighbors(const bh_grid* grid, int* offsets, int* neighbors, long lo
 int bh_candidates(const bh_plan* plan, const bh_grid* grid, const float* tmpl, const float* sub, int B, int L,
                   const int* tmpl_index, int n_templates, int S, float* starts_out, int* index_out,
                   float* grid_score_out, void* stream);
+
+/* ------------------------------------------------------------------ missing wedge */
+/*
+ * Missing-wedge constrained correlation (Sec. II-B: correlate only where both volumes sample Fourier
+ * space).  The subtomograms sample the directions |k_z| <= tan(a) |k_x| (tilt axis y, beam z, tilt
+ * half-angle a); the template is complete.  Rotating a subtomogram by R rotates that region, so the
+ * constrained score is C(R) = S(R) / sqrt(Dn(R)), Dn(R) = ||W_R t||^2, evaluated on the template's DFT
+ * samples 0 < |k| < N/2 (plus k = 0) with the wedge indicator expanded in spherical harmonics up to
+ * band L: Dn(R) = |T(0)|^2 + Re sum_{l<=L} sum_{m,m'} q_lm w_lm' D^l_{mm'}(R),
+ * q_lm = sum_k Y_l^m(k/|k|) |T(k)|^2 (T: DFT of the template restricted to the ball), w_lm = <Y_l^m, W>.
+ * bh_wedge_create prepares q and w on the host in FP64 (synchronous; about a second at 64^3) and keeps
+ * them on the plan's device.
+ *   tvol            host, N^3 floats: the template volume, layout [z][y][x]
+ *   half_angle_deg  a in (0, 90)
+ *   L               0..Lmax: the highest band the constrained alignment will use
+ */
+typedef struct bh_wedge bh_wedge;
+int bh_wedge_create(const bh_plan* plan, const float* tvol, double half_angle_deg, int L, bh_wedge** out);
+int bh_wedge_destroy(bh_wedge* wedge);
+/* Host FP64 copies: q and w as (L+1)^2 complex values, interleaved (re, im), slot l^2 + m + l; |T(0)|^2. */
+int bh_wedge_coeffs(const bh_wedge* wedge, double* q, double* w, double* c0);
+/* Dn(R) and its body-frame gradient at S rotations (device quats S*4, dn S floats, grad S*3 floats or
+   NULL), band L <= the wedge's. */
+int bh_wedge_norm(const bh_plan* plan, const bh_wedge* wedge, const float* quats, int S, int L, float* dn,
+                  float* grad, void* stream);
 
 /* ------------------------------------------------------------------ autotuning */
 typedef struct {

@@ -14,7 +14,8 @@ Readings where the paper is silent:
     S(R) of Eq. 2 and Dn(R) = ||W_R t||^2; ||f|| does not depend on R and is dropped.
   * Dn on the voxel grid: Dn(R) = |T(0)|^2 + sum over DFT frequencies 0 < |k| < N/2 of
     W_L(R^{-1} k/|k|) |T(k)|^2, T the unnormalised DFT of the template restricted to the ball, W_L the
-    spherical-harmonic expansion of W truncated at the marching band L (so Dn is band-limited like S).
+    spherical-harmonic expansion of W truncated at the marching band L of the stage (so Dn is
+    band-limited like S).
     Then Dn(R) = |T(0)|^2 + Re sum_{l<=L} sum_{m,m'} q_lm w_lm' D^l_{mm'}(R),
     q_lm = sum_k Y_l^m(k^) |T(k)|^2,  w_lm = <Y_l^m, W> on the sphere:
     Eq. 2's form with xi'^l_{mm'} = q_lm w_lm' (one radial index per degree).
@@ -114,7 +115,7 @@ def denominator(wd: Wedge, q, L: int) -> tuple[float, np.ndarray]:
 
 
 def constrained_score_grad(xi, wd: Wedge, q, L: int) -> tuple[float, np.ndarray]:
-    """C(R) = S(R) / sqrt(Dn(R)) and its body-frame gradient."""
+    """C(R) = S(R) / sqrt(Dn(R)) and its body-frame gradient, both at band L."""
     S, gS = score_grad(xi, q, L)
     Dn, gD = denominator(wd, q, L)
     r = 1.0 / math.sqrt(Dn)

@@ -23,7 +23,8 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
            "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
            "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_grid_create", "bh_grid_destroy", "bh_grid_info",
-           "bh_grid_neighbors", "bh_candidates", "bh_energy", "bh_autotune", "bh_autotune_newton", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
+           "bh_grid_neighbors", "bh_candidates", "bh_wedge_create", "bh_wedge_destroy", "bh_wedge_coeffs",
+           "bh_wedge_norm", "bh_energy", "bh_autotune", "bh_autotune_newton", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
            "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
@@ -41,7 +42,8 @@ class PlanOpts(ctypes.Structure):
 class AlignOpts(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int), ("tmpl_index", ctypes.c_void_p), ("n_templates", ctypes.c_int),
                 ("start_quat_out", ctypes.c_void_p), ("start_score_out", ctypes.c_void_p),
-                ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int), ("newton", ctypes.c_int)]
+                ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int), ("newton", ctypes.c_int),
+                ("wedge", ctypes.c_void_p)]
 
 
 _lib = None
@@ -74,6 +76,10 @@ def lib() -> ctypes.CDLL:
         L.bh_grid_info.argtypes = [vp, vp, vp, vp]
         L.bh_grid_neighbors.argtypes = [vp, vp, vp, ctypes.c_longlong]
         L.bh_candidates.argtypes = [vp, vp, vp, vp, i, i, vp, i, i, vp, vp, vp, vp]
+        L.bh_wedge_create.argtypes = [vp, vp, d, i, ctypes.POINTER(vp)]
+        L.bh_wedge_destroy.argtypes = [vp]
+        L.bh_wedge_coeffs.argtypes = [vp, vp, vp, vp]
+        L.bh_wedge_norm.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("bh_last_error", "bh_status_string"):
                 getattr(L, name).restype = i
@@ -209,7 +215,7 @@ def bh_score_hess(plan: Plan, tmpl, sub, quats, L: int, stream=None):
 # ------------------------------------------------------------------ alignment
 def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
                    n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None,
-                   refine_fp64: int = 0, starts_per_thread: int = 0, newton: bool = False):
+                   refine_fp64: int = 0, starts_per_thread: int = 0, newton: bool = False, wedge=None):
     """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
     import torch
     B, S = starts.shape[0], starts.shape[1]
@@ -225,6 +231,7 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     o.starts_per_thread = starts_per_thread
     o.refine_fp64 = refine_fp64
     o.newton = int(bool(newton))
+    o.wedge = wedge.handle if wedge is not None else None
     sq = ss = None
     if per_start or refine_fp64:
         sq = torch.empty((B, S, 4), dtype=torch.float32, device=dev)
@@ -326,6 +333,56 @@ def bh_candidates(plan: Plan, grid: Grid, tmpl, sub, L: int, S: int, tmpl_index=
     _check(lib().bh_candidates(plan.handle, grid.handle, _ptr(tmpl), _ptr(sub), B, L, _ptr(tmpl_index), n_templates,
                                S, _ptr(starts), _ptr(idx), _ptr(sc), _stream(stream)), "bh_candidates")
     return starts, idx, sc
+
+
+# ------------------------------------------------------------------ missing wedge
+class Wedge:
+    """Owning handle of a missing-wedge norm (bh_wedge_create)."""
+
+    def __init__(self, handle: int, L: int):
+        self.handle, self.L = handle, L
+
+    def coeffs(self):
+        """(q, w) as lists of (2l+1) complex arrays, and |T(0)|^2 (FP64 host copies)."""
+        n = (self.L + 1) ** 2
+        q = np.empty(2 * n)
+        w = np.empty(2 * n)
+        c0 = ctypes.c_double()
+        _check(lib().bh_wedge_coeffs(self.handle, q.ctypes.data, w.ctypes.data, ctypes.byref(c0)), "bh_wedge_coeffs")
+        qc, wc = q[0::2] + 1j * q[1::2], w[0::2] + 1j * w[1::2]
+        return ([qc[l * l:(l + 1) ** 2] for l in range(self.L + 1)], [wc[l * l:(l + 1) ** 2] for l in range(self.L + 1)],
+                c0.value)
+
+    def destroy(self):
+        if self.handle:
+            lib().bh_wedge_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def bh_wedge_create(plan: Plan, tvol: np.ndarray, half_angle_deg: float, L: int) -> Wedge:
+    v = np.ascontiguousarray(tvol, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(lib().bh_wedge_create(plan.handle, v.ctypes.data, float(half_angle_deg), int(L), ctypes.byref(h)),
+           "bh_wedge_create")
+    return Wedge(h.value, int(L))
+
+
+def bh_wedge_norm(plan: Plan, wedge: Wedge, quats, L: int, stream=None):
+    """Dn (S,) and its gradient (S, 3) at S rotations."""
+    import torch
+    S = quats.shape[0]
+    _need(quats, "torch.float32", S * 4, "quats")
+    dn = torch.empty((S,), dtype=torch.float32, device=quats.device)
+    g = torch.empty((S, 3), dtype=torch.float32, device=quats.device)
+    _check(lib().bh_wedge_norm(plan.handle, wedge.handle, _ptr(quats), S, L, _ptr(dn), _ptr(g), _stream(stream)),
+           "bh_wedge_norm")
+    return dn, g
 
 
 def bh_energy(plan: Plan, tmpl, sub, L: int, tmpl_index=None, n_templates: int = 0, stream=None):

@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libbh.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["plan.cpp", "expand.cu", "align.cu", "noalloc.cu", "serve.cpp"]
+SOURCES = ["plan.cpp", "expand.cu", "align.cu", "noalloc.cu", "serve.cpp", "wedge.cpp"]
 
 
 def nvcc() -> str:

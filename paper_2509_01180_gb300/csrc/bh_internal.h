@@ -18,6 +18,10 @@ namespace bh {
 int fail(int code, const char* fmt, ...);
 void clear_error();
 
+// Sphere-normalised associated Legendre functions with the Condon-Shortley phase, P[l * (L+1) + m] for
+// 0 <= m <= l <= L (Y_l^m = P_l^m(cos theta) e^{i m phi}); FP64, host.
+void legendre_all(int L, double x, double* P);
+
 #define BH_CUDA_TRY(call)                                                                           \
   do {                                                                                              \
     cudaError_t e_ = (call);                                                                        \
@@ -99,3 +103,17 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
 // align.cu
 int align_init_constants();
 }  // namespace bh
+
+// Common-region norm of the missing-wedge constrained correlation (bh_wedge_create): pseudo-coefficients
+// with one radial index per degree, so that the orbit-table evaluation of Eq. 2 yields
+// Dn(R) = |T(0)|^2 + Re sum_l sum_{m,m'} q_lm w_lm' D^l_{mm'}(R).
+struct bh_wedge {
+  int device = -1;
+  int L = 0;
+  double half_angle = 0.0;
+  bh::Layout layout{};          // K_l = 1, off_l = l^2, Lmax of the plan (indexes the plan's P table)
+  float2* d_t = nullptr;        // [(L+1)^2] conj(q_lm), |T(0)|^2 / w_00 added at l = 0
+  float2* d_w = nullptr;        // [(L+1)^2] w_lm
+  std::vector<double> q, w;     // host FP64 copies, interleaved (re, im), [(L+1)^2]
+  double c0 = 0.0;
+};

@@ -114,7 +114,7 @@ static void bessel_roots(int l, double lam_max, std::vector<double>& out) {
 //   Pbar_0^0 = 1/sqrt(4 pi); Pbar_m^m = -sqrt((2m+1)/(2m)) sqrt(1-x^2) Pbar_{m-1}^{m-1};
 //   Pbar_{m+1}^m = sqrt(2m+3) x Pbar_m^m;
 //   Pbar_l^m = a_lm (x Pbar_{l-1}^m - Pbar_{l-2}^m / a_{l-1,m}), a_lm = sqrt((4l^2-1)/(l^2-m^2)).
-static void legendre_all(int L, double x, double* P) {
+void legendre_all(int L, double x, double* P) {
   const int W = L + 1;
   const double s = std::sqrt(std::fmax(0.0, 1.0 - x * x));
   P[0] = 1.0 / std::sqrt(4.0 * M_PI);
