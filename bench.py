@@ -35,6 +35,12 @@ L2_FLUSH_BYTES = 256 << 20
 SMS, FMA_LANES = 152, 128
 
 
+# DRAM bytes per launch of the alignment kernel from an ncu capture of the same launch
+# (dram__bytes.sum.per_second x gpu__time_duration.sum), by (workload, subtomograms, (lanes, starts per
+# thread)); other shapes report no traffic.
+ALIGN_TRAFFIC_BYTES = {("batch32", 1024, (4, 2)): 25.36e6}
+
+
 def describe(w) -> str:
     m = w.meta
     parts = [f"{w.B} x {w.N}^3 subtomograms", f"{m['blobs']}-blob template sigma {m['sigma']}"]
@@ -643,8 +649,11 @@ def main():
             f_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
             peak = SMS * FMA_LANES * 2 * f_ghz * 1e9 / 1e12
             ach = fl / (per_step_aln / 1e3) / 1e12
+            tuned = (r["tune"]["align_group"], r["tune"]["align_starts_per_thread"])
+            traffic = ALIGN_TRAFFIC_BYTES.get((args.workload, B, tuned))
             roof = {"kernel": "k_align (bh_align_batch)", "bound": "alu", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                    "traffic_algorithmic": float(B) * r["Nb"] * 8 + float(B) * w.S * 16,
                     "peak_source": f"FP32 FMA: {SMS} SMs x {FMA_LANES} lanes x 2 flop x {f_ghz * 1e3:.0f} MHz"}
         else:
             mult = 3 if main_form == "bf16split" else 1
