@@ -460,7 +460,7 @@ def wedge_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
             "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 1}
 
 
-def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
+def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509, newton: bool = False) -> dict:
     """Continuous-batching server under a Poisson stream of requests (mean `rate` req/s for `seconds`):
     1-512 subtomograms per request (log-uniform), box edge uniform over {24, 32, 48, 64}, one of 8 resident
     templates (2 per box), 16 starts, bands N/8 -> N/4 -> N/2, 30 steps; noise (SNR 0.1) and a +-60 deg
@@ -473,7 +473,7 @@ def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
     boxes = [24, 32, 48, 64]
     t_setup = time.perf_counter()
     srv = bh.bh_serve_create(hbm_budget_bytes=48 << 30, max_inflight=4, max_batch=2048,
-                             mode=bh.BH_MODE_BF16_SPLIT, steps=30)
+                             mode=bh.BH_MODE_BF16_SPLIT, steps=8 if newton else 30, newton=newton)
     tids, pools = {}, {}
     for N in boxes:
         tpls = [synth.blob_template(synth.rng_for(40 + N, t), 60, 1.5 * N / 32, 0.75 * N / 2) for t in range(2)]
@@ -514,7 +514,8 @@ def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509) -> dict:
             "mean_subtomograms_per_request": total / max(1, len(subm)), "batches": int(st["batches"]),
             "setup_s": setup_s,
             "mix": "boxes 24/32/48/64 (l<=N/2, bands N/8-N/4-N/2), 1-512 subtomograms log-uniform, 16 starts, "
-                   "8 resident templates, SNR 0.1, +-60 deg wedge, BF16-split expansion"}
+                   "8 resident templates, SNR 0.1, +-60 deg wedge, BF16-split expansion",
+            "optimizer": "Newton steps, 8 per band" if newton else "gradient ascent, 30 steps per band"}
 
 
 def run_mixed(args, device, rank: int = 0, world: int = 1) -> dict:
@@ -589,6 +590,7 @@ def main():
     ap.add_argument("--refine", type=int, default=None, help="FP64 re-scoring of the K best starts (precision form)")
     ap.add_argument("--sec3", type=int, default=None,
                     help="also time the Sec. III protocol (candidates + Newton); default: on for batch32")
+    ap.add_argument("--serve-newton", type=int, default=1, help="also run the serving leg with Newton steps")
     ap.add_argument("--wedge-leg", type=int, default=None,
                     help="also time the missing-wedge constrained correlation; default: on for batch32")
     ap.add_argument("--sec3-grid", type=int, default=4608, help="rotation grid size for the candidate starts")
@@ -726,6 +728,8 @@ def main():
             line["cpu_baseline"] = base
         if world == 1 and args.serve_seconds > 0:
             line["serving"] = serving_leg(args.serve_seconds)
+            if args.serve_newton:
+                line["serving_newton"] = serving_leg(args.serve_seconds, newton=True)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -375,6 +375,8 @@ typedef struct {
   int queue_capacity;      /* requests waiting for admission; 0 = 65536 */
   int mode;                /* BH_MODE_* of the expansion for every box edge */
   int steps;               /* ascent steps per band; 0 = 30 */
+  int newton;              /* 0: gradient ascent (Sec. II-C); 1: damped Newton steps (Sec. III; fewer steps
+                              reach the same optimum, e.g. 8 per band) */
 } bh_serve_opts;
 
 typedef struct {

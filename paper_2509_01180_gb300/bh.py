@@ -423,7 +423,8 @@ def bh_autotune_newton(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
 
 class ServeOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int)]
+                ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int),
+                ("newton", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -528,9 +529,9 @@ class Server:
 
 
 def bh_serve_create(hbm_budget_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0, queue_capacity: int = 0,
-                    mode: int = BH_MODE_BF16_SPLIT, steps: int = 0) -> Server:
+                    mode: int = BH_MODE_BF16_SPLIT, steps: int = 0, newton: bool = False) -> Server:
     L = lib()
-    o = ServeOpts(hbm_budget_bytes, max_inflight, max_batch, queue_capacity, mode, steps)
+    o = ServeOpts(hbm_budget_bytes, max_inflight, max_batch, queue_capacity, mode, steps, int(bool(newton)))
     h = ctypes.c_void_p()
     _check(L.bh_serve_create(ctypes.byref(h), ctypes.byref(o)), "bh_serve_create")
     return Server(h.value)

@@ -158,6 +158,7 @@ int launch_batch(bh_server* s, Slot& sl, int N, int S) {
     bh_align_opts ao{};
     ao.tmpl_index = d_tidx;
     ao.n_templates = box.n_tmpl;
+    ao.newton = s->o.newton;
     rc = bh_align_batch(p, box.d_tmpl, d_coef, B, d_starts, S, box.stages, box.nstages, s->o.steps, d_quat, d_score,
                         &ao, st);
   }
@@ -296,6 +297,7 @@ extern "C" int bh_serve_create(bh_server** out, const bh_serve_opts* o) {
   if (opts.max_batch < 1 || opts.max_batch > 65536) return fail(BH_ERR_ARG, "max_batch %d", opts.max_batch);
   if (opts.queue_capacity < 1) return fail(BH_ERR_ARG, "queue_capacity %d", opts.queue_capacity);
   if (opts.steps < 0 || opts.steps > 100000) return fail(BH_ERR_ARG, "steps %d", opts.steps);
+  if (opts.newton != 0 && opts.newton != 1) return fail(BH_ERR_ARG, "newton %d not in {0,1}", opts.newton);
   if (opts.mode != BH_MODE_FP32 && opts.mode != BH_MODE_BF16_SPLIT) return fail(BH_ERR_ARG, "mode %d", opts.mode);
   int dev = 0;
   BH_CUDA_TRY(cudaGetDevice(&dev));

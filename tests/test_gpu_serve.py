@@ -123,3 +123,25 @@ def test_many_requests_overlap_and_report_latency(srv):
     assert st["batches"] - before >= 2
     p50, p99 = np.percentile(lat, [50, 99])
     assert 0 < p50 <= p99
+
+
+def test_newton_server_equals_batch_api():
+    """A server built with Newton steps returns what bh_align_batch with newton=True returns on the same inputs."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    s = bh.bh_serve_create(hbm_budget_bytes=1 << 30, max_inflight=2, max_batch=128, steps=8, newton=True)
+    N, B, S, seed = 16, 9, 8, 321
+    tpl = synth.blob_template(synth.rng_for(9, 12), 20, 1.2, 0.75 * N / 2)
+    tvol = synth.render(N, tpl).astype(np.float32)
+    tid = s.add_template(tvol)
+    vols = vols_for(N, B, 19)
+    q_srv, sc_srv, _ = s.wait(s.submit(tid, vols, S, seed=seed), timeout_ms=60000)
+    s.destroy()
+    plan = bh.bh_plan_create(N, N // 2, math.pi * N / 2, bh.BH_MODE_BF16_SPLIT)
+    dev = torch.device("cuda:0")
+    t = bh.bh_expand(plan, torch.from_numpy(tvol[None]).to(dev))[0].contiguous()
+    c = bh.bh_expand(plan, torch.from_numpy(vols).to(dev))
+    starts = torch.from_numpy(bh.bh_random_starts(seed, B, S)).to(dev)
+    q, sc = bh.bh_align_batch(plan, t, c, starts, [2, 4, 8], 8, newton=True)
+    assert np.array_equal(q.cpu().numpy(), q_srv) and np.array_equal(sc.cpu().numpy(), sc_srv)
+    plan.destroy()
