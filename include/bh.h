@@ -117,6 +117,18 @@ int bh_plan_layout(const bh_plan* plan, int* Nb, int* V, int* offsets);
 /* Options the plan was created with (lambda_max resolved). */
 int bh_plan_info(const bh_plan* plan, bh_plan_opts* opts);
 
+/*
+ * Error word of the plan's device waits.  Every wait of the tensor-core expansion pipeline (mbarrier
+ * phases between the TMA producer, the MMA issuer and the epilogue) gives up after about 2 s of device
+ * time, records the wait site and lets the kernel return, so a stalled pipeline never hangs the GPU.
+ * bh_plan_status returns BH_ERR_TIMEOUT (and clears the word) if that happened since the last check,
+ * else BH_OK; call it after synchronising the streams the plan's work ran on.  Synchronous.
+ * bh_plan_probe_wait enqueues a probe in which one such wait runs out (a barrier phase that nothing
+ * completes): about 2 s later bh_plan_status reports BH_ERR_TIMEOUT; the context stays usable.
+ */
+int bh_plan_status(bh_plan* plan);
+int bh_plan_probe_wait(bh_plan* plan, void* stream);
+
 /* ------------------------------------------------------------------ expansion */
 /*
  * Expansion display of Sec. II-A on the voxel grid: coeffs[b] = f_hat of vols[b].

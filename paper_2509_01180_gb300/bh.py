@@ -21,7 +21,7 @@ BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
-           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
+           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_plan_status", "bh_plan_probe_wait", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
            "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_grid_create", "bh_grid_destroy", "bh_grid_info",
            "bh_grid_neighbors", "bh_candidates", "bh_wedge_create", "bh_wedge_destroy", "bh_wedge_coeffs",
            "bh_wedge_norm", "bh_energy", "bh_autotune", "bh_autotune_newton", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
         L.bh_plan_destroy.argtypes = [vp]
         L.bh_plan_layout.argtypes = [vp, vp, vp, vp]
         L.bh_plan_info.argtypes = [vp, ctypes.POINTER(PlanOpts)]
+        L.bh_plan_status.argtypes = [vp]
+        L.bh_plan_probe_wait.argtypes = [vp, vp]
         L.bh_expand.argtypes = [vp, vp, i, vp, vp]
         L.bh_expand_noalloc.argtypes = [vp, vp, i, vp, vp]
         L.bh_score_grad.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp]
@@ -170,6 +172,16 @@ def bh_plan_layout(plan: Plan):
 
 
 # ------------------------------------------------------------------ expansion
+def bh_plan_status(plan: Plan) -> None:
+    """Raise BHError(BH_ERR_TIMEOUT) if a device wait of the plan's work gave up since the last check."""
+    _check(lib().bh_plan_status(plan.handle), "bh_plan_status")
+
+
+def bh_plan_probe_wait(plan: Plan, stream=None) -> None:
+    """Enqueue a probe in which a bounded device wait runs out (about 2 s)."""
+    _check(lib().bh_plan_probe_wait(plan.handle, _stream(stream)), "bh_plan_probe_wait")
+
+
 def bh_expand(plan: Plan, vols, coeffs=None, stream=None):
     """vols: CUDA float32 (B, N, N, N); returns coeffs: CUDA float32 (B, Nb, 2) (complex interleaved)."""
     import torch

@@ -1428,6 +1428,7 @@ static int check_common(const bh_plan* p, const float* tmpl, const float* sub, i
 extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* quats, int S,
                              int L, float* score, float* grad, void* stream) {
   clear_error();
+  const bh::Range range_("bh_score_grad");
   int st = check_common(p, tmpl, sub, B, quats, S);
   if (st != BH_OK) return st;
   if (L < 0 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 0..%d", L, p->Lmax);
@@ -1452,6 +1453,7 @@ extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* s
 extern "C" int bh_score_hess(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* quats, int S,
                              int L, float* score, float* grad, float* hess, void* stream) {
   clear_error();
+  const bh::Range range_("bh_score_hess");
   int st = check_common(p, tmpl, sub, B, quats, S);
   if (st != BH_OK) return st;
   if (L < 0 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 0..%d", L, p->Lmax);
@@ -1476,6 +1478,7 @@ extern "C" int bh_score_hess(const bh_plan* p, const float* tmpl, const float* s
 extern "C" int bh_wedge_norm(const bh_plan* p, const bh_wedge* w, const float* quats, int S, int L, float* dn,
                              float* grad, void* stream) {
   clear_error();
+  const bh::Range range_("bh_wedge_norm");
   if (!p || !w) return fail(BH_ERR_ARG, "plan or wedge is NULL");
   if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d outside 1..%d", S, kMaxThreads);
   if (L < 0 || L > w->L) return fail(BH_ERR_ARG, "L=%d outside 0..%d (wedge band)", L, w->L);
@@ -1500,6 +1503,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
                               const int* stages, int nstages, int steps, float* quat_out, float* score_out,
                               const bh_align_opts* opts, void* stream) {
   clear_error();
+  const bh::Range range_("bh_align_batch");
   int st = check_common(p, tmpl, sub, B, starts, S);
   if (st != BH_OK) return st;
   if (!stages || nstages < 1 || nstages > kMaxStages) return fail(BH_ERR_ARG, "nstages=%d outside 1..%d", nstages, kMaxStages);
@@ -1587,6 +1591,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
 
 extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out) {
   clear_error();
+  const bh::Range range_("bh_autotune");
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
   if (B < 1 || B > (1 << 20)) return fail(BH_ERR_ARG, "B=%d", B);
   if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d", S);
@@ -1698,6 +1703,7 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
 extern "C" int bh_autotune_newton(bh_plan* p, int B, int S, const int* stages, int nstages, int steps,
                                   bh_tune_result* out) {
   clear_error();
+  const bh::Range range_("bh_autotune_newton");
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
   if (B < 1 || B > (1 << 20)) return fail(BH_ERR_ARG, "B=%d", B);
   if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d", S);
@@ -1771,6 +1777,7 @@ extern "C" int bh_autotune_newton(bh_plan* p, int B, int S, const int* stages, i
 extern "C" int bh_energy(const bh_plan* p, const float* tmpl, const float* sub, int B, int L, const int* tmpl_index,
                          int n_templates, float* energy, void* stream) {
   clear_error();
+  const bh::Range range_("bh_energy");
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
   if (B < 0 || L < 0 || L > p->Lmax) return fail(BH_ERR_ARG, "B=%d L=%d", B, L);
   if (B == 0) return BH_OK;
@@ -1825,6 +1832,7 @@ extern "C" int bh_align_shifts(bh_plan* p, const float* tmpl, const float* vols,
                                size_t workspace_bytes, int* shift_out, float* quat_out, float* score_out,
                                const bh_align_opts* opts, void* stream_) {
   clear_error();
+  const bh::Range range_("bh_align_shifts");
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
   if (B < 0 || nshift < 1 || nshift > 4096 || S < 1) return fail(BH_ERR_ARG, "B=%d nshift=%d S=%d", B, nshift, S);
   if (B == 0) return BH_OK;
@@ -2058,6 +2066,7 @@ size_t grid_smem(int L, int n, int npow2, int S) {
 
 extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double radius) {
   clear_error();
+  const bh::Range range_("bh_grid_create");
   if (!out) return fail(BH_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!quats) return fail(BH_ERR_ARG, "quats is NULL");
@@ -2134,6 +2143,7 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
                              const int* tmpl_index, int n_templates, int S, float* starts_out, int* index_out,
                              float* grid_score_out, void* stream) {
   clear_error();
+  const bh::Range range_("bh_candidates");
   if (!p || !grid) return fail(BH_ERR_ARG, "plan or grid is NULL");
   if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
   if (L < 1 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 1..%d", L, p->Lmax);

@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bh.h"
 
 namespace bh {
@@ -17,6 +19,14 @@ namespace bh {
 // Record a message for bh_last_error() and return `code`.
 int fail(int code, const char* fmt, ...);
 void clear_error();
+
+// NVTX range spanning a C-ABI call (shown on profiler timelines; a no-op without an attached tool).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Sphere-normalised associated Legendre functions with the Condon-Shortley phase, P[l * (L+1) + m] for
 // 0 <= m <= l <= L (Y_l^m = P_l^m(cos theta) e^{i m phi}); FP64, host.

@@ -659,8 +659,44 @@ int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, i
 
 using namespace bh;
 
+namespace bh {
+namespace {
+// Probe of the bounded mbarrier wait used by the tensor-core pipeline: one thread waits on a phase that
+// nothing completes; after the wait's time limit it records `code` in the error word and returns, as a
+// stalled GEMM pipeline would.
+__global__ void k_wait_probe(int* err, int code) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_wait(&bar, 0u, err, code);
+  }
+}
+}  // namespace
+}  // namespace bh
+
+extern "C" int bh_plan_status(bh_plan* p) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  int code = 0;
+  BH_CUDA_TRY(cudaMemcpy(&code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code == 0) return BH_OK;
+  BH_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  return fail(BH_ERR_TIMEOUT, "a device wait gave up (site %d); the results of the plan's work since the last "
+              "status check are invalid", code);
+}
+
+extern "C" int bh_plan_probe_wait(bh_plan* p, void* stream) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  bh::k_wait_probe<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(p->d_err, 199);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
 extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, void* stream_) {
   clear_error();
+  const bh::Range range_("bh_expand");
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
   if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
   if (B == 0) return BH_OK;

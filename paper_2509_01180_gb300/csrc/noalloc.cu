@@ -48,6 +48,7 @@ int scratch_address(void** out) {
 
 extern "C" int bh_expand_noalloc(bh_plan* p, const float* vols, int B, float* coeffs, void* stream) {
   bh::clear_error();
+  const bh::Range range_("bh_expand_noalloc");
   if (!p) return bh::fail(BH_ERR_ARG, "plan is NULL");
   if (B < 0) return bh::fail(BH_ERR_ARG, "B=%d", B);
   if (B == 0) return BH_OK;

@@ -215,6 +215,7 @@ static void free_plan(bh_plan* p) {
 
 extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   clear_error();
+  const bh::Range range_("bh_plan_create");
   if (!out || !o) return fail(BH_ERR_ARG, "NULL argument");
   *out = nullptr;
   if (o->N < 4 || o->N > 256 || (o->N % 2)) return fail(BH_ERR_ARG, "N=%d must be even in 4..256", o->N);

@@ -101,6 +101,7 @@ struct bh_server {
 namespace {
 
 int launch_batch(bh_server* s, Slot& sl, int N, int S) {
+  const bh::Range range_("bh_serve batch");
   Box& box = s->boxes[N];
   bh_plan* p = box.plan;
   int B = 0;

@@ -99,6 +99,7 @@ extern "C" int bh_wedge_destroy(bh_wedge* w) {
 
 extern "C" int bh_wedge_create(const bh_plan* p, const float* tvol, double half_angle_deg, int L, bh_wedge** out) {
   clear_error();
+  const bh::Range range_("bh_wedge_create");
   if (!out) return fail(BH_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (!p || !tvol) return fail(BH_ERR_ARG, "plan or template is NULL");
