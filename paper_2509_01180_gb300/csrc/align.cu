@@ -992,11 +992,6 @@ struct Cx64 {
 };
 __device__ __forceinline__ Cx64 cm64(Cx64 a, Cx64 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 __device__ __forceinline__ Cx64 cj64(Cx64 a) { return {a.x, -a.y}; }
-__device__ __forceinline__ Cx64 cp64(Cx64 a, int k) {
-  Cx64 r{1.0, 0.0};
-  for (int i = 0; i < k; ++i) r = cm64(r, a);
-  return r;
-}
 
 __device__ __forceinline__ Cx64 cpow64(Cx64 a, int k) {  // a^k, k >= 0, by binary exponentiation
   Cx64 r{1.0, 0.0};
