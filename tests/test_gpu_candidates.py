@@ -86,7 +86,7 @@ def _pair16_case(dev, count, L1):
     return w, Bs, p, c, t, F
 
 
-@pytest.mark.parametrize("n,S", [(1000, 8), (37, 37), (300, 1)])
+@pytest.mark.parametrize("n,S", [(1000, 8), (37, 37), (300, 1), (300, 100)])  # S > 64: the sort path
 def test_candidates_match_oracle(dev, n, S):
     L1, radius = 4, math.radians(50.0 if n >= 300 else 80.0)
     w, Bs, p, c, t, F = _pair16_case(dev, 3, L1)

@@ -108,7 +108,7 @@ def test_align_batch_guards(dev, B, S, group, spt, newton, refine):
     p.destroy()
 
 
-@pytest.mark.parametrize("n,S", [(37, 1), (37, 37), (1000, 5)])
+@pytest.mark.parametrize("n,S", [(37, 1), (37, 37), (1000, 5), (300, 100)])
 def test_candidate_guards(dev, n, S):
     p = _plan()
     t, sub = _coeffs(p, dev, 3)

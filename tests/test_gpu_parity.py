@@ -470,3 +470,57 @@ def test_newton_batch32_sample(dev):
         if ang >= 0.1 and not tied:
             fails.append((b, ang))
     assert not fails, fails
+
+
+# ---------------------------------------------------------------------------- full-size launches, sampled
+@pytest.mark.slow
+def test_batch32_full_launch_sampled(dev):
+    """The bench's main launch (1024 x 32^3, BF16-split expansion, autotuned alignment variant): sampled
+    subtomograms against the oracle's expansion and ascent from the same starts (0.1 degree unless tied)."""
+    w = synth.make_workload("batch32")
+    p = bh.bh_plan_create(w.N, w.Lmax, w.lam_max, bh.BH_MODE_BF16_SPLIT, max_batch=1024)
+    bh.bh_autotune(p, w.B, w.S, w.stages, w.steps)
+    tmpl = bh.bh_expand(p, torch.from_numpy(w.template[None]).to(dev))[0].contiguous()
+    coef = bh.bh_expand(p, torch.from_numpy(w.vols).to(dev))
+    q, s = bh.bh_align_batch(p, tmpl, coef, torch.from_numpy(w.starts).to(dev), w.stages, w.steps)
+    q, s = q.cpu().numpy().astype(np.float64), s.cpu().numpy()
+    Bs = basis_for(32, 16)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    sample = [0, 517, 1023]
+    F = ball.expand(Bs, w.vols[sample].astype(np.float64))
+    for j, b in enumerate(sample):
+        ref = align.align_particle(Bs, t, F[j], w.starts[b].astype(np.float64), w.stages, w.steps)
+        srt = np.sort(ref.start_score)[::-1]
+        tied = (srt[0] - srt[1]) < 1e-4 * abs(srt[0])
+        ang = math.degrees(wigner.geodesic_angle(q[b] / np.linalg.norm(q[b]), ref.q))
+        assert tied or ang < 0.1, (b, ang)
+        assert abs(float(s[b]) - ref.score) < 1e-4 * abs(ref.score) or tied
+    p.destroy()
+
+
+@pytest.mark.slow
+def test_precision64_full_launch_sampled(dev):
+    """The precision form's launch (4096 x 64^3, BF16-split expansion, FP64 re-score of the best 4 starts;
+    256 distinct phantoms tiled): for sampled subtomograms the reported score is the oracle's FP64 Eq. 2 at
+    the reported rotation, on the oracle's own coefficients, within the score tolerance
+    1e-4 ||t|| ||f|| (the GPU's coefficients carry the split's ~5e-6 error), and the rotation is within
+    2 degrees of the ground truth."""
+    w = synth.make_workload("precision64", count=256)
+    rep = np.arange(4096) % 256
+    p = bh.bh_plan_create(w.N, w.Lmax, w.lam_max, bh.BH_MODE_BF16_SPLIT, max_batch=4096)
+    tmpl = bh.bh_expand(p, torch.from_numpy(w.template[None]).to(dev))[0].contiguous()
+    coef = bh.bh_expand(p, torch.from_numpy(np.ascontiguousarray(w.vols[rep])).to(dev))
+    starts = torch.from_numpy(np.ascontiguousarray(w.starts[rep])).to(dev)
+    q, s = bh.bh_align_batch(p, tmpl, coef, starts, w.stages, w.steps, refine_fp64=4)
+    q, s = q.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+    p.destroy()
+    del coef
+    Bs = basis_for(64, 32)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    for b in (7, 4095):
+        f = ball.expand(Bs, w.vols[rep[b]][None].astype(np.float64))[0]
+        xi = align.build_xi(Bs, t, f, 32)
+        qb = q[b] / np.linalg.norm(q[b])
+        ref = align.score(xi, qb, 32)
+        assert abs(s[b] - ref) < 1e-4 * np.linalg.norm(t) * np.linalg.norm(f), (b, s[b], ref)
+        assert math.degrees(wigner.geodesic_angle(qb, wigner.quat_conj(w.q_true[rep[b]]))) < 2.0
