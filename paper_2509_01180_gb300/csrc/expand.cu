@@ -103,6 +103,28 @@ __global__ void k_to_complex(const float* __restrict__ C, int ldc, int B, int Nb
   out[(size_t)b * Nb + s] = make_float2(re, im);
 }
 
+// The same, one CTA per row: the row's split partial sums are added (in split order) into shared memory with
+// coalesced loads, then the complex coefficients are formed from shared memory.  Bitwise equal to
+// k_to_complex (a negated sum equals the sum of the negated terms).
+__global__ void __launch_bounds__(256) k_to_complex_rows(const float* __restrict__ C, int ldc, int Nb,
+                                                         const int2* __restrict__ slot, float2* __restrict__ out,
+                                                         int splits, size_t split_stride) {
+  extern __shared__ float row[];
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < ldc; c += blockDim.x) {
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += C[(size_t)z * split_stride + (size_t)b * ldc + c];
+    row[c] = v;
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < Nb; s += blockDim.x) {
+    const int2 src = slot[s];
+    const float re = src.x > 0 ? row[src.x - 1] : (src.x < 0 ? -row[-src.x - 1] : 0.f);
+    const float im = src.y > 0 ? row[src.y - 1] : (src.y < 0 ? -row[-src.y - 1] : 0.f);
+    out[(size_t)b * Nb + s] = make_float2(re, im);
+  }
+}
+
 // ---------------------------------------------------------------- plain FP32 GEMM, both operands K-major
 // C[M][N] = A[M][K] * B[N][K]^T; M % 128 == 0, N % 128 == 0, K % 16 == 0.
 constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16, SG_PAD = 4;
@@ -549,12 +571,45 @@ int set_gemm_bn(bh_plan* p, int bn) {
 // K splits for a pass of Mp rows: enough CTAs for about two waves over the SMs when the output tiles
 // alone are few, each split keeping at least 32 K-blocks (two promotion chunks), at most the plan's
 // scratch allows.
+// Split-K count of a pass: one GEMM CTA is resident per SM, so take the fewest splits whose last wave of
+// CTAs is at least 90 % full (else the fullest), keeping at least 32 K-blocks per split.
 static int choose_splits(const bh_plan* p, int Mp) {
   const int tiles = (Mp / kGemmBM) * (p->Nb_pad / 128);
   const int num_kb = p->V_pad / kGemmBK;
-  int s = (2 * p->num_sms + tiles - 1) / tiles;
-  s = std::min(s, std::max(1, num_kb / 32));
-  return std::max(1, std::min(s, p->ksplit_max));
+  const int smax = std::max(1, std::min(p->ksplit_max, num_kb / 32));
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= smax; ++s) {
+    const double waves = (double)tiles * s / p->num_sms;
+    const double eff = waves / std::ceil(waves);
+    if (eff >= 0.9) return s;
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+// Complex coefficients of `rows` GEMM rows (split partial sums added in order).
+static int launch_to_complex(const bh_plan* p, const float* C, int rows, float* coeffs, int splits, size_t stride,
+                             cudaStream_t stream) {
+  const size_t row_bytes = (size_t)p->Nb_pad * sizeof(float);
+  if (row_bytes <= 96 * 1024) {
+    static bool attr = false;
+    if (!attr) {
+      BH_CUDA_TRY(cudaFuncSetAttribute(k_to_complex_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+      attr = true;
+    }
+    k_to_complex_rows<<<rows, 256, row_bytes, stream>>>(C, p->Nb_pad, p->Nb, p->d_slot, reinterpret_cast<float2*>(coeffs),
+                                                        splits, stride);
+  } else {
+    dim3 g2((p->Nb + 255) / 256, rows);
+    k_to_complex<<<g2, 256, 0, stream>>>(C, p->Nb_pad, rows, p->Nb, p->d_slot, reinterpret_cast<float2*>(coeffs),
+                                         splits, stride);
+  }
+  BH_CHECK_LAUNCH();
+  return BH_OK;
 }
 
 static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
@@ -618,10 +673,8 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
                                                           num_kb, num_kb, 0, p->d_err);
     }
     BH_CHECK_LAUNCH();
-    dim3 g2((p->Nb + 255) / 256, Bc);
-    k_to_complex<<<g2, 256, 0, stream>>>(scratch_c, p->Nb_pad, Bc, p->Nb, p->d_slot,
-                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb, 1, 0);
-    BH_CHECK_LAUNCH();
+    const int st = launch_to_complex(p, scratch_c, Bc, coeffs + (size_t)b0 * p->Nb * 2, 1, 0, stream);
+    if (st != BH_OK) return st;
   }
   return BH_OK;
 }
@@ -646,11 +699,9 @@ int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, i
                                round_up((p->V_pad + splits - 1) / splits, SG_BK)
                          : (nkb + round_up((nkb + splits - 1) / splits, KCHUNK) - 1) /
                                round_up((nkb + splits - 1) / splits, KCHUNK);
-    dim3 g2((p->Nb + 255) / 256, rows);
-    k_to_complex<<<g2, 256, 0, stream>>>(p->d_C, p->Nb_pad, rows, p->Nb, p->d_slot,
-                                         reinterpret_cast<float2*>(coeffs) + (size_t)r0 * p->Nb, used,
-                                         (size_t)p->M_cap * p->Nb_pad);
-    BH_CHECK_LAUNCH();
+    st = launch_to_complex(p, p->d_C, rows, coeffs + (size_t)r0 * p->Nb * 2, used, (size_t)p->M_cap * p->Nb_pad,
+                           stream);
+    if (st != BH_OK) return st;
   }
   return BH_OK;
 }
@@ -719,11 +770,9 @@ extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, vo
                                round_up((p->V_pad + splits - 1) / splits, SG_BK)
                          : (nkb + round_up((nkb + splits - 1) / splits, KCHUNK) - 1) /
                                round_up((nkb + splits - 1) / splits, KCHUNK);
-    dim3 g2((p->Nb + 255) / 256, Bc);
-    k_to_complex<<<g2, 256, 0, stream>>>(p->d_C, p->Nb_pad, Bc, p->Nb, p->d_slot,
-                                         reinterpret_cast<float2*>(coeffs) + (size_t)b0 * p->Nb, used,
-                                         (size_t)p->M_cap * p->Nb_pad);
-    BH_CHECK_LAUNCH();
+    st = launch_to_complex(p, p->d_C, Bc, coeffs + (size_t)b0 * p->Nb * 2, used, (size_t)p->M_cap * p->Nb_pad,
+                           stream);
+    if (st != BH_OK) return st;
   }
   return BH_OK;
 }
