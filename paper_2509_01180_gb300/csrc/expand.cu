@@ -40,19 +40,46 @@ __global__ void k_build_table(const double* __restrict__ radial, int n_r2, const
 }
 
 // ---------------------------------------------------------------- gather in-ball voxels (+ hi/lo split)
-__global__ void k_gather(const float* __restrict__ vols, int B, long long N3, const int* __restrict__ vox, int V,
-                         int V_pad, float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
-                         __nv_bfloat16* __restrict__ Xlo) {
+// Row b of X = the in-ball voxels of volume b (zero beyond V and for padding rows), as FP32 or as a BF16
+// hi/lo split (x = hi + lo to ~2^-16).  Four consecutive voxels per thread (V_pad is a multiple of 64):
+// one 16-byte index load, four independent gathers, one 16-byte (FP32) or two 8-byte (BF16) stores.
+__global__ void k_gather4(const float* __restrict__ vols, int B, long long N3, const int* __restrict__ vox, int V,
+                          int V_pad, float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
+                          __nv_bfloat16* __restrict__ Xlo) {
   const int b = blockIdx.y;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (v >= V_pad) return;
-  const float x = (b < B && v < V) ? __ldg(vols + (size_t)b * N3 + vox[v]) : 0.0f;
+  float x[4] = {0.f, 0.f, 0.f, 0.f};
+  if (b < B) {
+    const float* vb = vols + (size_t)b * N3;
+    if (v + 4 <= V) {
+      const int4 id = __ldg(reinterpret_cast<const int4*>(vox + v));
+      x[0] = __ldg(vb + id.x);
+      x[1] = __ldg(vb + id.y);
+      x[2] = __ldg(vb + id.z);
+      x[3] = __ldg(vb + id.w);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (v + u < V) x[u] = __ldg(vb + vox[v + u]);
+    }
+  }
   const size_t o = (size_t)b * V_pad + v;
-  if (X32) X32[o] = x;
+  if (X32) *reinterpret_cast<float4*>(X32 + o) = make_float4(x[0], x[1], x[2], x[3]);
   if (Xhi) {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-    Xhi[o] = hi;
-    Xlo[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      hi[u] = __float2bfloat16_rn(x[u]);
+      lo[u] = __float2bfloat16_rn(x[u] - __bfloat162float(hi[u]));
+    }
+    uint2 ph, pl;
+    ph.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
+    ph.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
+    pl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
+    pl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
+    *reinterpret_cast<uint2*>(Xhi + o) = ph;
+    *reinterpret_cast<uint2*>(Xlo + o) = pl;
   }
 }
 
@@ -658,8 +685,8 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
   for (int b0 = 0; b0 < B; b0 += rows_cap) {
     const int Bc = std::min(rows_cap, B - b0);
     const int Mp = round_up(Bc, kGemmBM);
-    dim3 g1((p->V_pad + 255) / 256, Mp);
-    k_gather<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
+    dim3 g1((p->V_pad / 4 + 255) / 256, Mp);
+    k_gather4<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
     BH_CHECK_LAUNCH();
     if (p->mode == BH_MODE_FP32) {
       dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN);
@@ -757,9 +784,9 @@ extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, vo
   for (int b0 = 0; b0 < B; b0 += p->max_batch) {
     const int Bc = std::min(p->max_batch, B - b0);
     const int Mp = round_up(Bc, kGemmBM);
-    dim3 g1((p->V_pad + 255) / 256, Mp);
-    k_gather<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, p->d_X32, p->d_Xhi,
-                                     p->d_Xlo);
+    dim3 g1((p->V_pad / 4 + 255) / 256, Mp);
+    k_gather4<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, p->d_X32, p->d_Xhi,
+                                      p->d_Xlo);
     BH_CHECK_LAUNCH();
     const int splits = choose_splits(p, Mp);
     int st = launch_gemm(p, Mp, splits, stream);
