@@ -190,6 +190,28 @@ def test_align_groups_agree(dev, group):
     assert math.degrees(wigner.geodesic_angle(q / np.linalg.norm(q), ref.q)) < 0.1
 
 
+@pytest.mark.parametrize("group", [2, 4, 8, 16])
+def test_align_two_starts_per_thread_agree(dev, group):
+    """Two starts advanced per thread (shared table loads) change only rounding: the oracle's optimum, and
+    the oracle's optimum of every start that converged to a clear maximum."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = oracle_align(w, 0, Bs, t, f)
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    q, s, sq, _ = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev),
+                                    torch.from_numpy(w.starts).to(dev), w.stages, w.steps, group=group,
+                                    starts_per_thread=2, per_start=True)
+    q = q.cpu().numpy()[0].astype(np.float64)
+    assert math.degrees(wigner.geodesic_angle(q / np.linalg.norm(q), ref.q)) < 0.1
+    assert abs(float(s[0]) - ref.score) < 1e-4 * abs(ref.score)
+    sq = sq.cpu().numpy()[0].astype(np.float64)
+    agree = [math.degrees(wigner.geodesic_angle(sq[i] / np.linalg.norm(sq[i]), ref.start_q[i])) < 0.1
+             for i in range(w.S)]
+    assert sum(agree) >= w.S - 1
+
+
 @pytest.mark.parametrize("mode", [bh.BH_MODE_FP32, bh.BH_MODE_BF16_SPLIT])
 def test_full_path_pair16(dev, mode):
     """Voxels -> GPU expansion -> GPU alignment vs the same in FP64; recovers R_true^{-1}."""
