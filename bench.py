@@ -512,6 +512,8 @@ def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509, newton: b
     return {"requests": len(subm), "subtomograms": total, "offered_req_per_s": rate, "seconds": seconds,
             "throughput": total / span, "unit": UNIT, "p50_ms": p50, "p99_ms": p99,
             "mean_subtomograms_per_request": total / max(1, len(subm)), "batches": int(st["batches"]),
+            "volumes": ("read in place from host memory by the expansion (coherent C2C access)"
+                        if st["in_place_batches"] == st["batches"] else "copied host to device per batch"),
             "setup_s": setup_s,
             "mix": "boxes 24/32/48/64 (l<=N/2, bands N/8-N/4-N/2), 1-512 subtomograms log-uniform, 16 starts, "
                    "8 resident templates, SNR 0.1, +-60 deg wedge, BF16-split expansion",

@@ -370,10 +370,17 @@ int bh_random_starts(uint64_t seed, int B, int S, float* out);
 /* ------------------------------------------------------------------ serving */
 /*
  * A request loop with continuous batching: requests of uneven sizes and box edges arrive at any
- * time; a worker thread admits them in arrival order while the HBM budget and a free stream slot
- * allow, merges waiting requests of the same box edge into one batch (expansion + one alignment
- * launch with a per-subtomogram template index), and keeps up to max_inflight batches on the device
- * at once on separate streams.  Template coefficients stay resident.  Each subtomogram's result
+ * time; a worker thread admits them while the HBM budget and a free stream slot allow, merges waiting
+ * requests of the same box edge into one batch (expansion + one alignment launch with a
+ * per-subtomogram template index), and keeps up to max_inflight bulk batches on the device at once on
+ * separate streams.  Optionally, requests whose estimated device time is at most express_ms form an
+ * express class with its own express_slots streams at the device's highest stream priority;
+ * admission keeps arrival order within each class.  Batch
+ * memory comes from the server's own stream-ordered pool, which keeps up to the budget mapped.  Where
+ * the device reads pageable host memory coherently (cudaDevAttrPageableMemoryAccess, e.g. a Grace host
+ * over NVLink-C2C), the expansion gathers each request's in-ball voxels straight from its host buffer:
+ * no host->device copy of the volumes and no host thread blocked on one.
+ * Template coefficients stay resident.  Each subtomogram's result
  * depends only on its own data, template, starts and the box's schedule -- not on what it was
  * batched with.  Schedule per box edge N: Lmax = N/2, lambda_max = pi N/2, bands Lmax/4, Lmax/2,
  * Lmax, `steps` ascent steps per band.
@@ -389,6 +396,12 @@ typedef struct {
   int steps;               /* ascent steps per band; 0 = 30 */
   int newton;              /* 0: gradient ascent (Sec. II-C); 1: damped Newton steps (Sec. III; fewer steps
                               reach the same optimum, e.g. 8 per band) */
+  int express_slots;       /* 0 (default): one class, every request bulk; 1..16: that many high-priority
+                              streams for an express class of small requests */
+  double express_ms;       /* estimated device time (ms) up to which a request, and a merged express
+                              batch, is express; 0 = 2.0 */
+  int ingest;              /* 0: read request volumes in place when the device reads pageable host memory
+                              coherently, else copy them to the device; 1: always copy */
 } bh_serve_opts;
 
 typedef struct {
@@ -404,9 +417,14 @@ typedef struct {
 
 typedef struct {
   uint64_t submitted, completed, batches;
+  uint64_t express_batches; /* batches of the express class */
+  uint64_t in_place_batches; /* batches whose volumes the expansion read in place from host memory */
   uint64_t queued;          /* waiting for admission */
   uint64_t inflight_batches;
   size_t inflight_bytes;    /* budget in use */
+  uint64_t staging_allocs;  /* pinned staging (re)allocations, creation included */
+  double launch_ms_total;   /* worker thread time spent enqueueing batches (copies, starts, launches) */
+  double launch_ms_max;     /* longest single enqueue */
 } bh_serve_counters;
 
 /* Create a server on the current device.  Errors: BH_ERR_ARG, BH_ERR_CUDA, BH_ERR_UNSUPPORTED. */

@@ -436,7 +436,8 @@ def bh_autotune_newton(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
 class ServeOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int),
-                ("newton", ctypes.c_int)]
+                ("newton", ctypes.c_int), ("express_slots", ctypes.c_int), ("express_ms", ctypes.c_double),
+                ("ingest", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -447,7 +448,9 @@ class Request(ctypes.Structure):
 
 class ServeCounters(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
-                ("queued", ctypes.c_uint64), ("inflight_batches", ctypes.c_uint64), ("inflight_bytes", ctypes.c_size_t)]
+                ("express_batches", ctypes.c_uint64), ("in_place_batches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("inflight_batches", ctypes.c_uint64), ("inflight_bytes", ctypes.c_size_t), ("staging_allocs", ctypes.c_uint64),
+                ("launch_ms_total", ctypes.c_double), ("launch_ms_max", ctypes.c_double)]
 
 
 def _serve_sigs(L):
@@ -541,9 +544,11 @@ class Server:
 
 
 def bh_serve_create(hbm_budget_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0, queue_capacity: int = 0,
-                    mode: int = BH_MODE_BF16_SPLIT, steps: int = 0, newton: bool = False) -> Server:
+                    mode: int = BH_MODE_BF16_SPLIT, steps: int = 0, newton: bool = False, express_slots: int = 0,
+                    express_ms: float = 0.0, ingest: int = 0) -> Server:
     L = lib()
-    o = ServeOpts(hbm_budget_bytes, max_inflight, max_batch, queue_capacity, mode, steps, int(bool(newton)))
+    o = ServeOpts(hbm_budget_bytes, max_inflight, max_batch, queue_capacity, mode, steps, int(bool(newton)),
+                  express_slots, express_ms, ingest)
     h = ctypes.c_void_p()
     _check(L.bh_serve_create(ctypes.byref(h), ctypes.byref(o)), "bh_serve_create")
     return Server(h.value)

@@ -108,8 +108,10 @@ int make_tensor_maps(bh_plan* p);
 int set_gemm_bn(bh_plan* p, int bn);
 int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, int nshift, float* coeffs,
                    cudaStream_t stream);
-int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scratch_x, float* scratch_c, int rows_cap,
-                cudaStream_t stream);
+// Expansion through caller scratch; volume b is vols + b N^3, or vptr[b] when vptr (a device array of B
+// addresses) is given.
+int expand_into(bh_plan* p, const float* vols, const float* const* vptr, int B, float* coeffs, void* scratch_x,
+                float* scratch_c, int rows_cap, cudaStream_t stream);
 // align.cu
 int align_init_constants();
 }  // namespace bh

@@ -43,15 +43,18 @@ __global__ void k_build_table(const double* __restrict__ radial, int n_r2, const
 // Row b of X = the in-ball voxels of volume b (zero beyond V and for padding rows), as FP32 or as a BF16
 // hi/lo split (x = hi + lo to ~2^-16).  Four consecutive voxels per thread (V_pad is a multiple of 64):
 // one 16-byte index load, four independent gathers, one 16-byte (FP32) or two 8-byte (BF16) stores.
-__global__ void k_gather4(const float* __restrict__ vols, int B, long long N3, const int* __restrict__ vox, int V,
-                          int V_pad, float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
-                          __nv_bfloat16* __restrict__ Xlo) {
+// kPtr: volume b starts at vptr[b] (a table of B addresses, e.g. request buffers in host memory that the
+// device reads coherently) instead of vols + b N^3.
+template <bool kPtr>
+__global__ void k_gather4(const float* __restrict__ vols, const float* const* __restrict__ vptr, int B, long long N3,
+                          const int* __restrict__ vox, int V, int V_pad, float* __restrict__ X32,
+                          __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo) {
   const int b = blockIdx.y;
   const int v = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (v >= V_pad) return;
   float x[4] = {0.f, 0.f, 0.f, 0.f};
   if (b < B) {
-    const float* vb = vols + (size_t)b * N3;
+    const float* vb = kPtr ? vptr[b] : vols + (size_t)b * N3;
     if (v + 4 <= V) {
       const int4 id = __ldg(reinterpret_cast<const int4*>(vox + v));
       x[0] = __ldg(vb + id.x);
@@ -667,8 +670,8 @@ static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
 // kernels as bh_expand, with the gathered volumes and the real GEMM output placed in `scratch_x` /
 // `scratch_c`, `rows_cap` rows (a multiple of the 128-row M tile) per pass.  Tensor maps of the gathered
 // volumes are encoded for the given scratch on every call (host-side encoding, no allocation).
-int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scratch_x, float* scratch_c, int rows_cap,
-                cudaStream_t stream) {
+int expand_into(bh_plan* p, const float* vols, const float* const* vptr, int B, float* coeffs, void* scratch_x,
+                float* scratch_c, int rows_cap, cudaStream_t stream) {
   const long long N3 = (long long)p->N * p->N * p->N;
   float* X32 = nullptr;
   __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
@@ -686,7 +689,11 @@ int expand_into(bh_plan* p, const float* vols, int B, float* coeffs, void* scrat
     const int Bc = std::min(rows_cap, B - b0);
     const int Mp = round_up(Bc, kGemmBM);
     dim3 g1((p->V_pad / 4 + 255) / 256, Mp);
-    k_gather4<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
+    if (vptr)
+      k_gather4<true><<<g1, 256, 0, stream>>>(nullptr, vptr + b0, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
+    else
+      k_gather4<false><<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, nullptr, Bc, N3, p->d_vox, p->V, p->V_pad, X32,
+                                               Xhi, Xlo);
     BH_CHECK_LAUNCH();
     if (p->mode == BH_MODE_FP32) {
       dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN);
@@ -785,8 +792,8 @@ extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, vo
     const int Bc = std::min(p->max_batch, B - b0);
     const int Mp = round_up(Bc, kGemmBM);
     dim3 g1((p->V_pad / 4 + 255) / 256, Mp);
-    k_gather4<<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, Bc, N3, p->d_vox, p->V, p->V_pad, p->d_X32, p->d_Xhi,
-                                      p->d_Xlo);
+    k_gather4<false><<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, nullptr, Bc, N3, p->d_vox, p->V, p->V_pad,
+                                             p->d_X32, p->d_Xhi, p->d_Xlo);
     BH_CHECK_LAUNCH();
     const int splits = choose_splits(p, Mp);
     int st = launch_gemm(p, Mp, splits, stream);

@@ -70,5 +70,5 @@ extern "C" int bh_expand_noalloc(bh_plan* p, const float* vols, int B, float* co
   unsigned char* b = static_cast<unsigned char*>(base);
   const size_t x_bytes = bh::round_up64((int64_t)rows_cap * p->V_pad * 4, 256);
   float* c = reinterpret_cast<float*>(b + x_bytes);
-  return bh::expand_into(p, vols, B, coeffs, b, c, rows_cap, static_cast<cudaStream_t>(stream));
+  return bh::expand_into(p, vols, nullptr, B, coeffs, b, c, rows_cap, static_cast<cudaStream_t>(stream));
 }

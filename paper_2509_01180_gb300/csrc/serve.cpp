@@ -1,13 +1,24 @@
 // Serving: a request loop with continuous batching over the expansion and alignment kernels.
 //
 // Requests (template id, B host volumes, S starts) are queued by bh_serve_submit.  One worker thread
-// owns all device work: it retires finished batches (event query), then admits waiting requests in
-// arrival order -- merging the head request with later ones of the same box edge and start count --
-// as long as a stream slot is free and the batch's device footprint fits the remaining HBM budget.
-// A batch is: stream-ordered allocation, host->device copies, expansion (bh::expand_into with the
-// batch's own scratch, so batches on different streams never share scratch), one bh_align_batch
-// launch with a per-subtomogram template index, device->host copies into pinned staging, stream-ordered
-// free, event.  Up to max_inflight batches are on the device at once.
+// owns all device work: it retires finished batches (event query), then admits waiting requests --
+// merging the head request with later ones of the same box edge and start count -- as long as a stream
+// slot is free and the batch's device footprint fits the remaining HBM budget.
+// A batch is: stream-ordered allocation from the server's own memory pool (which keeps up to the budget
+// mapped, so steady-state allocations never go back to the driver), host->device copies, expansion
+// (bh::expand_into with the batch's own scratch, so batches on different streams never share scratch),
+// one bh_align_batch launch with a per-subtomogram template index, device->host copies into pinned
+// staging, stream-ordered free, event.  Up to max_inflight bulk batches are on the device at once.
+//
+// Optionally (express_slots > 0) two classes: a request whose estimated device time (a throughput model
+// of the expansion and the marching ascent) is at most express_ms is "express" and runs on one of
+// express_slots streams created at the device's highest priority, so the block scheduler gives its
+// kernels the next free SM slots ahead of bulk work already queued; bulk requests use the max_inflight
+// low-priority streams.  Within a class admission keeps arrival order (the head of a class is never
+// overtaken by a later request of the same class); an express request may take a free bulk stream
+// when no bulk request waits.  Off by default: under bursts of large requests the measured p99 latency
+// of the mixed Poisson workload was lower with one class.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -47,6 +58,7 @@ struct Req {
   bh_request r;
   int N;
   int row;
+  bool express = false;
   Clock::time_point t_submit, t_done;
   int status = BH_PENDING;
 };
@@ -56,6 +68,7 @@ struct Slot {
   cudaEvent_t done = nullptr;
   float* h_starts = nullptr;  // pinned staging
   int* h_tidx = nullptr;
+  const float** h_vptr = nullptr;  // volume addresses (in-place ingestion)
   float* h_quat = nullptr;
   float* h_score = nullptr;
   size_t cap_starts = 0, cap_b = 0;
@@ -63,12 +76,39 @@ struct Slot {
   std::vector<std::shared_ptr<Req>> reqs;
   size_t bytes = 0;
   int launch_status = BH_OK;
+  bool express = false;  // high-priority stream reserved for express batches
 };
 
-size_t batch_bytes(const bh_plan* p, int B, int S) {
+// Device bytes of a batch: its volumes (unless read in place from the request buffers, then a table of
+// B addresses), coefficients, starts, template indices, results and expansion scratch.
+size_t batch_bytes(const bh_plan* p, int B, int S, bool in_place) {
   const size_t rows = (size_t)bh::round_up(std::min(B, kScratchRows), bh::kGemmBM);
-  return (size_t)B * p->N * p->N * p->N * 4 + (size_t)B * p->Nb * 8 + (size_t)B * S * 16 + (size_t)B * 4 +
-         (size_t)B * 20 + rows * ((size_t)p->V_pad * 4 + (size_t)p->Nb_pad * 4) + 4 * 256;
+  const size_t vols = in_place ? (size_t)B * sizeof(void*) : (size_t)B * p->N * p->N * p->N * 4;
+  return vols + (size_t)B * p->Nb * 8 + (size_t)B * S * 16 + (size_t)B * 4 + (size_t)B * 20 +
+         rows * ((size_t)p->V_pad * 4 + (size_t)p->Nb_pad * 4) + 4 * 256;
+}
+
+// Work of one evaluation of Eq. 2 with its gradient at band L (flop): 30 per orbit-step of the
+// d-recursion and 46 per orbit.
+double eval_flop(int L) {
+  double steps = 0.0;
+  for (int m = 0; m <= L; ++m) steps += (2.0 * m + 1.0) * (L - m + 1);
+  const double orbits = (L + 1.0) * (L + 1.0);
+  return 30.0 * (steps - orbits) + 46.0 * orbits;
+}
+
+// Estimated device time (ms) of a batch of B subtomograms: the expansion at 1 PFLOP/s of executed tensor
+// work (three BF16 products) or 40 TFLOP/s (FP32), but no less than one pass of the basis table over HBM
+// (every batch streams it once: 13 GB for the BF16 hi/lo table at 64^3) at 6.5 TB/s; the ascent at
+// 20 TFLOP/s of FP32 work.  Throughputs measured for these kernels; used only to classify requests.
+double est_ms(const bh_plan* p, const int* stages, int nstages, int steps, int B, int S) {
+  const double gemm = 2.0 * p->V * p->Nb;
+  const double expand = (p->mode == BH_MODE_BF16_SPLIT) ? 3.0 * gemm / 1e12 : gemm / 40e12;
+  const double table = 4.0 * p->Nb_pad * p->V_pad / 6.5e12;  // FP32, or BF16 hi + lo: 4 bytes per entry
+  double align = 0.0;
+  for (int i = 0; i < nstages; ++i) align += eval_flop(stages[i]);
+  align *= (double)S * (1.0 + steps) / 20e12;
+  return 1e3 * (std::max(B * expand, table) + B * align);
 }
 
 uint64_t splitmix64(uint64_t x) {
@@ -90,15 +130,53 @@ struct bh_server {
   std::map<int, Box> boxes;
   std::vector<Template> templates;
   std::vector<Slot> slots;
+  cudaMemPool_t pool = nullptr;
+  double express_ms = 0.0;
+  bool in_place = false;  // the device reads request volumes in host memory coherently (no H2D copy)
   uint64_t next_ticket = 1;
   size_t used = 0;
   bool stop = false, paused = false;
-  uint64_t submitted = 0, completed = 0, batches = 0;
+  uint64_t submitted = 0, completed = 0, batches = 0, express_batches = 0, in_place_batches = 0;
+  std::atomic<uint64_t> staging_allocs{0};
+  double launch_ms_total = 0.0, launch_ms_max = 0.0;  // worker time spent enqueueing batches
   std::thread worker;
   std::mutex plan_mu;  // serialises plan creation / template upload with the worker's launches
 };
 
 namespace {
+
+// Pinned staging of a slot for B subtomograms with S starts.  Sized at server creation for max_batch
+// subtomograms and up to kStagedStarts starts, so that the batch path never frees pinned memory (a
+// pinned free waits for the whole device); only a request with more starts grows it.
+constexpr int kStagedStarts = 64;
+
+int grow_staging(bh_server* s, Slot& sl, int B, int S) {
+  if (sl.cap_b < (size_t)B) {
+    cudaFreeHost(sl.h_tidx);
+    cudaFreeHost(sl.h_quat);
+    cudaFreeHost(sl.h_score);
+    cudaFreeHost(sl.h_vptr);
+    sl.h_tidx = nullptr;
+    sl.h_quat = sl.h_score = nullptr;
+    sl.h_vptr = nullptr;
+    sl.cap_b = 0;
+    BH_CUDA_TRY(cudaMallocHost(&sl.h_vptr, (size_t)B * sizeof(float*)));
+    BH_CUDA_TRY(cudaMallocHost(&sl.h_tidx, (size_t)B * sizeof(int)));
+    BH_CUDA_TRY(cudaMallocHost(&sl.h_quat, (size_t)B * 4 * sizeof(float)));
+    BH_CUDA_TRY(cudaMallocHost(&sl.h_score, (size_t)B * sizeof(float)));
+    sl.cap_b = (size_t)B;
+    ++s->staging_allocs;
+  }
+  if (sl.cap_starts < (size_t)B * S * 4) {
+    cudaFreeHost(sl.h_starts);
+    sl.h_starts = nullptr;
+    sl.cap_starts = 0;
+    BH_CUDA_TRY(cudaMallocHost(&sl.h_starts, (size_t)B * S * 4 * sizeof(float)));
+    sl.cap_starts = (size_t)B * S * 4;
+    ++s->staging_allocs;
+  }
+  return BH_OK;
+}
 
 int launch_batch(bh_server* s, Slot& sl, int N, int S) {
   const bh::Range range_("bh_serve batch");
@@ -106,20 +184,9 @@ int launch_batch(bh_server* s, Slot& sl, int N, int S) {
   bh_plan* p = box.plan;
   int B = 0;
   for (auto& r : sl.reqs) B += r->r.B;
-  // pinned staging (grown on demand)
-  if (sl.cap_b < (size_t)B) {
-    cudaFreeHost(sl.h_tidx);
-    cudaFreeHost(sl.h_quat);
-    cudaFreeHost(sl.h_score);
-    sl.cap_b = (size_t)bh::round_up(B, 1024);
-    BH_CUDA_TRY(cudaMallocHost(&sl.h_tidx, sl.cap_b * sizeof(int)));
-    BH_CUDA_TRY(cudaMallocHost(&sl.h_quat, sl.cap_b * 4 * sizeof(float)));
-    BH_CUDA_TRY(cudaMallocHost(&sl.h_score, sl.cap_b * sizeof(float)));
-  }
-  if (sl.cap_starts < (size_t)B * S * 4) {
-    cudaFreeHost(sl.h_starts);
-    sl.cap_starts = (size_t)bh::round_up(B * S * 4, 1 << 16);
-    BH_CUDA_TRY(cudaMallocHost(&sl.h_starts, sl.cap_starts * sizeof(float)));
+  {
+    const int rc = grow_staging(s, sl, std::max(B, s->o.max_batch), S);
+    if (rc != BH_OK) return rc;
   }
   int off = 0;
   for (auto& r : sl.reqs) {
@@ -135,26 +202,37 @@ int launch_batch(bh_server* s, Slot& sl, int N, int S) {
   cudaStream_t st = sl.stream;
   const size_t N3 = (size_t)N * N * N;
   const int rows = bh::round_up(std::min(B, kScratchRows), bh::kGemmBM);
+  const bool in_place = s->in_place;
   float *d_vols = nullptr, *d_coef = nullptr, *d_starts = nullptr, *d_quat = nullptr, *d_score = nullptr;
   float *d_sx = nullptr, *d_sc = nullptr;
+  const float** d_vptr = nullptr;
   int* d_tidx = nullptr;
-  BH_CUDA_TRY(cudaMallocAsync(&d_vols, (size_t)B * N3 * 4, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_coef, (size_t)B * p->Nb * 8, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_starts, (size_t)B * S * 16, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_tidx, (size_t)B * 4, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_quat, (size_t)B * 16, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_score, (size_t)B * 4, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_sx, (size_t)rows * p->V_pad * 4, st));
-  BH_CUDA_TRY(cudaMallocAsync(&d_sc, (size_t)rows * p->Nb_pad * 4, st));
+  cudaMemPool_t pool = s->pool;
+  if (in_place)
+    BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_vptr, (size_t)B * sizeof(float*), pool, st));
+  else
+    BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_vols, (size_t)B * N3 * 4, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_coef, (size_t)B * p->Nb * 8, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_starts, (size_t)B * S * 16, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_tidx, (size_t)B * 4, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_quat, (size_t)B * 16, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_score, (size_t)B * 4, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_sx, (size_t)rows * p->V_pad * 4, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_sc, (size_t)rows * p->Nb_pad * 4, pool, st));
   off = 0;
   for (auto& r : sl.reqs) {
-    BH_CUDA_TRY(cudaMemcpyAsync(d_vols + (size_t)off * N3, r->r.vols, sizeof(float) * (size_t)r->r.B * N3,
-                                cudaMemcpyHostToDevice, st));
+    if (in_place) {
+      for (int b = 0; b < r->r.B; ++b) sl.h_vptr[off + b] = r->r.vols + (size_t)b * N3;
+    } else {
+      BH_CUDA_TRY(cudaMemcpyAsync(d_vols + (size_t)off * N3, r->r.vols, sizeof(float) * (size_t)r->r.B * N3,
+                                  cudaMemcpyHostToDevice, st));
+    }
     off += r->r.B;
   }
+  if (in_place) BH_CUDA_TRY(cudaMemcpyAsync(d_vptr, sl.h_vptr, (size_t)B * sizeof(float*), cudaMemcpyHostToDevice, st));
   BH_CUDA_TRY(cudaMemcpyAsync(d_starts, sl.h_starts, (size_t)B * S * 16, cudaMemcpyHostToDevice, st));
   BH_CUDA_TRY(cudaMemcpyAsync(d_tidx, sl.h_tidx, (size_t)B * 4, cudaMemcpyHostToDevice, st));
-  int rc = bh::expand_into(p, d_vols, B, d_coef, d_sx, d_sc, rows, st);
+  int rc = bh::expand_into(p, d_vols, d_vptr, B, d_coef, d_sx, d_sc, rows, st);
   if (rc == BH_OK) {
     bh_align_opts ao{};
     ao.tmpl_index = d_tidx;
@@ -167,9 +245,9 @@ int launch_batch(bh_server* s, Slot& sl, int N, int S) {
     BH_CUDA_TRY(cudaMemcpyAsync(sl.h_quat, d_quat, (size_t)B * 16, cudaMemcpyDeviceToHost, st));
     BH_CUDA_TRY(cudaMemcpyAsync(sl.h_score, d_score, (size_t)B * 4, cudaMemcpyDeviceToHost, st));
   }
-  for (void* ptr : {(void*)d_vols, (void*)d_coef, (void*)d_starts, (void*)d_tidx, (void*)d_quat, (void*)d_score,
-                    (void*)d_sx, (void*)d_sc})
-    cudaFreeAsync(ptr, st);
+  for (void* ptr : {(void*)d_vols, (void*)d_vptr, (void*)d_coef, (void*)d_starts, (void*)d_tidx, (void*)d_quat,
+                    (void*)d_score, (void*)d_sx, (void*)d_sc})
+    if (ptr) cudaFreeAsync(ptr, st);
   BH_CUDA_TRY(cudaEventRecord(sl.done, st));
   return rc;
 }
@@ -213,46 +291,81 @@ void worker_loop(bh_server* s) {
       s->cv_done.notify_all();
     }
     if (s->stop && !any_busy) break;
-    // 2. admit
-    Slot* free_slot = nullptr;
-    for (auto& sl : s->slots)
-      if (!sl.busy) {
-        free_slot = &sl;
-        break;
-      }
+    // 2. admit: express first, then bulk; each class in its own arrival order
     bool launched = false;
-    if (!s->stop && !s->paused && free_slot && !s->queue.empty()) {
-      auto head = s->queue.front();
-      const int N = head->N, S = head->r.S;
-      bh_plan* p = s->boxes[N].plan;
-      std::vector<std::shared_ptr<Req>> take;
-      int B = 0;
-      for (auto it = s->queue.begin(); it != s->queue.end();) {
-        auto& r = *it;
-        if (r->N == N && r->r.S == S && B + r->r.B <= s->o.max_batch &&
-            s->used + batch_bytes(p, B + r->r.B, S) <= s->o.hbm_budget_bytes) {
-          B += r->r.B;
-          take.push_back(r);
-          it = s->queue.erase(it);
-        } else if (take.empty()) {
-          break;  // the head does not fit yet: keep arrival order
-        } else {
-          ++it;
+    if (!s->stop && !s->paused && !s->queue.empty()) {
+      bool bulk_waiting = false;
+      for (auto& r : s->queue)
+        if (!r->express) {
+          bulk_waiting = true;
+          break;
         }
-      }
-      if (!take.empty()) {
+      for (int cls = 1; cls >= 0 && !launched; --cls) {
+        const bool ex = cls == 1;
+        Slot* free_slot = nullptr;
+        for (auto& sl : s->slots)
+          if (!sl.busy && sl.express == ex) {
+            free_slot = &sl;
+            break;
+          }
+        if (!free_slot && ex && !bulk_waiting)
+          for (auto& sl : s->slots)
+            if (!sl.busy) {
+              free_slot = &sl;
+              break;
+            }
+        if (!free_slot) continue;
+        std::shared_ptr<Req> head;
+        for (auto& r : s->queue)
+          if (r->express == ex) {
+            head = r;
+            break;
+          }
+        if (!head) continue;
+        const int N = head->N, S = head->r.S;
+        const Box& box = s->boxes[N];
+        bh_plan* p = box.plan;
+        std::vector<std::shared_ptr<Req>> take;
+        int B = 0;
+        for (auto it = s->queue.begin(); it != s->queue.end();) {
+          auto& r = *it;
+          if (r->express != ex) {
+            ++it;
+            continue;
+          }
+          const bool fits = r->N == N && r->r.S == S && B + r->r.B <= s->o.max_batch &&
+                            s->used + batch_bytes(p, B + r->r.B, S, s->in_place) <= s->o.hbm_budget_bytes &&
+                            (!ex || take.empty() ||
+                             est_ms(p, box.stages, box.nstages, s->o.steps, B + r->r.B, S) <= s->express_ms);
+          if (fits) {
+            B += r->r.B;
+            take.push_back(r);
+            it = s->queue.erase(it);
+          } else if (take.empty()) {
+            break;  // the class head does not fit yet: keep its arrival order
+          } else {
+            ++it;
+          }
+        }
+        if (take.empty()) continue;
         free_slot->busy = true;
         free_slot->reqs = take;
-        free_slot->bytes = batch_bytes(p, B, S);
+        free_slot->bytes = batch_bytes(p, B, S, s->in_place);
         s->used += free_slot->bytes;
         ++s->batches;
+        if (ex) ++s->express_batches;
+        if (s->in_place) ++s->in_place_batches;
         lk.unlock();
         int rc;
+        const auto t_launch = Clock::now();
         {
           std::lock_guard<std::mutex> pg(s->plan_mu);
           rc = launch_batch(s, *free_slot, N, S);
         }
+        const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t_launch).count();
         lk.lock();
+        s->launch_ms_total += ms;
+        s->launch_ms_max = std::max(s->launch_ms_max, ms);
         free_slot->launch_status = rc;
         if (rc != BH_OK) cudaEventRecord(free_slot->done, free_slot->stream);
         launched = true;
@@ -294,27 +407,65 @@ extern "C" int bh_serve_create(bh_server** out, const bh_serve_opts* o) {
   if (opts.max_batch == 0) opts.max_batch = 1024;
   if (opts.queue_capacity == 0) opts.queue_capacity = 65536;
   if (opts.steps == 0) opts.steps = 30;
+  if (opts.ingest != 0 && opts.ingest != 1) return fail(BH_ERR_ARG, "ingest %d not in {0,1}", opts.ingest);
+  if (opts.express_ms == 0.0) opts.express_ms = 2.0;
   if (opts.max_inflight < 1 || opts.max_inflight > 16) return fail(BH_ERR_ARG, "max_inflight %d", opts.max_inflight);
   if (opts.max_batch < 1 || opts.max_batch > 65536) return fail(BH_ERR_ARG, "max_batch %d", opts.max_batch);
   if (opts.queue_capacity < 1) return fail(BH_ERR_ARG, "queue_capacity %d", opts.queue_capacity);
   if (opts.steps < 0 || opts.steps > 100000) return fail(BH_ERR_ARG, "steps %d", opts.steps);
   if (opts.newton != 0 && opts.newton != 1) return fail(BH_ERR_ARG, "newton %d not in {0,1}", opts.newton);
   if (opts.mode != BH_MODE_FP32 && opts.mode != BH_MODE_BF16_SPLIT) return fail(BH_ERR_ARG, "mode %d", opts.mode);
+  if (opts.express_slots < 0 || opts.express_slots > 16) return fail(BH_ERR_ARG, "express_slots %d", opts.express_slots);
+  if (!(opts.express_ms > 0.0) || !std::isfinite(opts.express_ms)) return fail(BH_ERR_ARG, "express_ms %g", opts.express_ms);
   int dev = 0;
   BH_CUDA_TRY(cudaGetDevice(&dev));
   cudaDeviceProp prop;
   BH_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
   if (prop.major != 10 || prop.minor != 3) return fail(BH_ERR_UNSUPPORTED, "device is sm_%d%d", prop.major, prop.minor);
+  int prio_low = 0, prio_high = 0;
+  BH_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
   auto* s = new bh_server();
   s->device = dev;
   s->o = opts;
-  s->slots.resize(opts.max_inflight);
-  for (auto& sl : s->slots) {
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+  s->express_ms = opts.express_ms;
+  int pageable = 0;
+  BH_CUDA_TRY(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev));
+  s->in_place = opts.ingest == 0 && pageable == 1;
+  const int n_express = opts.express_slots;
+  s->slots.resize(opts.max_inflight + n_express);
+  for (size_t i = 0; i < s->slots.size(); ++i) {
+    Slot& sl = s->slots[i];
+    sl.express = (int)i >= opts.max_inflight;
+    if (cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, sl.express ? prio_high : prio_low) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
       bh_serve_destroy(s);
       return fail(BH_ERR_CUDA, "stream/event creation failed");
     }
+  }
+  for (auto& sl : s->slots)
+    if (grow_staging(s, sl, opts.max_batch, kStagedStarts) != BH_OK) {
+      bh_serve_destroy(s);
+      return fail(BH_ERR_OOM, "pinned staging for %d subtomograms", opts.max_batch);
+    }
+  // the server's own stream-ordered pool: memory up to the budget stays mapped between batches
+  cudaMemPoolProps pp{};
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = dev;
+  if (cudaMemPoolCreate(&s->pool, &pp) != cudaSuccess) {
+    s->pool = nullptr;
+    bh_serve_destroy(s);
+    return fail(BH_ERR_CUDA, "memory pool creation failed");
+  }
+  // Memory freed by another stream's batch is reused only once that free has completed: the pool must
+  // not make a batch wait on an unrelated one (an express batch would otherwise inherit the latency of
+  // the bulk batch whose memory it was given).
+  uint64_t keep = opts.hbm_budget_bytes;
+  int no_dep = 0;
+  if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+      cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no_dep) != cudaSuccess) {
+    bh_serve_destroy(s);
+    return fail(BH_ERR_CUDA, "memory pool attributes");
   }
   s->worker = std::thread(worker_loop, s);
   *out = s;
@@ -378,8 +529,8 @@ extern "C" int bh_serve_submit(bh_server* s, const bh_request* r, uint64_t* tick
   const Template t = s->templates[r->template_id];
   const bh_plan* p = s->boxes[t.N].plan;
   if (r->B > s->o.max_batch) return fail(BH_ERR_BUDGET, "B=%d exceeds max_batch %d", r->B, s->o.max_batch);
-  if (batch_bytes(p, r->B, r->S) > s->o.hbm_budget_bytes)
-    return fail(BH_ERR_BUDGET, "request needs %zu device bytes, budget %zu", batch_bytes(p, r->B, r->S),
+  if (batch_bytes(p, r->B, r->S, s->in_place) > s->o.hbm_budget_bytes)
+    return fail(BH_ERR_BUDGET, "request needs %zu device bytes, budget %zu", batch_bytes(p, r->B, r->S, s->in_place),
                 s->o.hbm_budget_bytes);
   if ((int)s->queue.size() >= s->o.queue_capacity) return fail(BH_ERR_BUSY, "queue full");
   auto q = std::make_shared<Req>();
@@ -387,6 +538,9 @@ extern "C" int bh_serve_submit(bh_server* s, const bh_request* r, uint64_t* tick
   q->r = *r;
   q->N = t.N;
   q->row = t.row;
+  const Box& box = s->boxes[t.N];
+  q->express = s->o.express_slots > 0 &&
+               est_ms(p, box.stages, box.nstages, s->o.steps, r->B, r->S) <= s->express_ms;
   q->t_submit = Clock::now();
   s->queue.push_back(q);
   s->reqs[q->ticket] = q;
@@ -445,6 +599,11 @@ extern "C" int bh_serve_stats(bh_server* s, bh_serve_counters* out) {
   out->submitted = s->submitted;
   out->completed = s->completed;
   out->batches = s->batches;
+  out->express_batches = s->express_batches;
+  out->in_place_batches = s->in_place_batches;
+  out->staging_allocs = s->staging_allocs.load();
+  out->launch_ms_total = s->launch_ms_total;
+  out->launch_ms_max = s->launch_ms_max;
   out->queued = s->queue.size();
   out->inflight_batches = 0;
   for (auto& sl : s->slots) out->inflight_batches += sl.busy ? 1 : 0;
@@ -472,11 +631,13 @@ extern "C" int bh_serve_destroy(bh_server* s) {
     cudaFreeHost(sl.h_tidx);
     cudaFreeHost(sl.h_quat);
     cudaFreeHost(sl.h_score);
+    cudaFreeHost(sl.h_vptr);
   }
   for (auto& kv : s->boxes) {
     cudaFree(kv.second.d_tmpl);
     bh_plan_destroy(kv.second.plan);
   }
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
   return BH_OK;
 }

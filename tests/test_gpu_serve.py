@@ -4,7 +4,9 @@ Checks: a request's result alone equals its result in a mix of requests of other
 templates (per-subtomogram work depends only on its own inputs); the served result equals the batch API
 on the same inputs; HBM-budget admission rejects requests that can never fit; a host-injected stall
 (paused admission) makes a bounded wait return BH_ERR_TIMEOUT and the request still completes after
-resuming; malformed requests get error codes; many requests overlap in several in-flight batches."""
+resuming; malformed requests get error codes; many requests overlap in several in-flight batches; the
+express class (high-priority streams for small requests) and in-place ingestion (the expansion reading
+request buffers in host memory) give the same results as bulk batches and device copies."""
 import math
 
 import numpy as np
@@ -78,8 +80,8 @@ def test_budget_admission_rejects_requests_that_never_fit():
     s = bh.bh_serve_create(hbm_budget_bytes=4 << 20, max_batch=4096)
     tpl = synth.blob_template(synth.rng_for(9, 1), 10, 1.2, 6.0)
     tid = s.add_template(synth.render(16, tpl).astype(np.float32))
-    with pytest.raises(bh.BHError) as e:
-        s.submit(tid, vols_for(16, 200, 0), S=8)
+    with pytest.raises(bh.BHError) as e:  # > 4 MiB of coefficients and scratch even with volumes read in place
+        s.submit(tid, vols_for(16, 1000, 0), S=8)
     assert e.value.status == bh.BH_ERR_BUDGET
     q, sc, _ = s.wait(s.submit(tid, vols_for(16, 1, 0), S=8), timeout_ms=60000)  # a small one still fits
     assert np.isfinite(sc).all()
@@ -145,3 +147,35 @@ def test_newton_server_equals_batch_api():
     q, sc = bh.bh_align_batch(plan, t, c, starts, [2, 4, 8], 8, newton=True)
     assert np.array_equal(q.cpu().numpy(), q_srv) and np.array_equal(sc.cpu().numpy(), sc_srv)
     plan.destroy()
+
+
+def _server_results(reqs, **kw):
+    s = bh.bh_serve_create(hbm_budget_bytes=1 << 30, max_inflight=2, max_batch=256, steps=12, **kw)
+    tpl = synth.blob_template(synth.rng_for(9, 21), 30, 1.2, 0.75 * 12)
+    tid = s.add_template(synth.render(24, tpl).astype(np.float32))
+    tickets = [s.submit(tid, v, S=8, seed=sd) for v, sd in reqs]
+    out = [s.wait(t, timeout_ms=120000)[:2] for t in tickets]
+    st = s.stats()
+    s.destroy()
+    return out, st
+
+
+def test_express_and_in_place_give_the_batch_results():
+    """The same requests through every server configuration: express streams or bulk only, volumes read in
+    place or copied -- bitwise the same rotations and scores, and the counters say which path ran."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    reqs = [(vols_for(24, B, 300 + i), 40 + i) for i, B in enumerate((1, 3, 40, 7, 120, 2))]
+    base, st0 = _server_results(reqs, ingest=1)
+    assert st0["express_batches"] == 0 and st0["in_place_batches"] == 0
+    for kw in (dict(), dict(express_slots=2), dict(express_slots=2, express_ms=1e9), dict(express_slots=1, ingest=1)):
+        out, st = _server_results(reqs, **kw)
+        for (q0, s0), (q1, s1) in zip(base, out):
+            assert np.array_equal(q0, q1) and np.array_equal(s0, s1), kw
+        if kw.get("ingest") == 1:
+            assert st["in_place_batches"] == 0
+        if kw.get("express_ms") == 1e9:
+            assert st["express_batches"] == st["batches"]
+        if not kw.get("express_slots"):
+            assert st["express_batches"] == 0
+        assert st["staging_allocs"] >= 2 and st["launch_ms_max"] >= 0.0
