@@ -174,10 +174,14 @@ struct Eval {
 // the evaluation is shared: (C starts of one subtomogram): each orbit-step loads the
 // table entry, the per-band constants and the rational coefficient g once and advances C independent
 // recursions, so the shared part of the step is paid once per C starts and every thread carries C
-// independent FMA chains.
-template <int G, int C>
-__device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
-                               const float* __restrict__ lbin, Eval (&out)[C]) {
+// independent FMA chains.  With T = 2 the same rotations are scored against a second table of the same
+// band (tab2; out[j * T + 1]): the d-recursion, seeds and phases -- functions of the rotation only -- are
+// computed once and only the accumulations against the table entries are repeated.  Results for each
+// table are bitwise those of a separate evaluation (the same operations in the same order).
+template <int G, int C, int T = 1>
+__device__ void eval_rotations(const float4* __restrict__ tab, const float4* __restrict__ tab2, int Lb, int L,
+                               const float4 (&q)[C], int qg, const float* __restrict__ lbin, Eval (&out)[C * T]) {
+  static_assert(T == 1 || T == 2, "one or two tables");
   float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
   float2 es[C], ed[C], R1[C], R2[C], Ed2[C], Uq[C], Wrow[C];
 #pragma unroll
@@ -203,55 +207,75 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
     Uq[j] = cpow(Es, qg);
     Wrow[j] = cpow(ed[j], qg);
   }
-  float S[C], Sa[C], Sb[C], Sg[C];
+  constexpr int CT = C * T;  // accumulator sets: start j, table k at j * T + k
+  float S[CT], Sa[CT], Sb[CT], Sg[CT];
 #pragma unroll
-  for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
+  for (int j = 0; j < CT; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
   for (int m = 0; m <= L; ++m) {
     const int w = 2 * m + 1;
     const float4* rowp = tab + tab_base(m, Lb);
+    const float4* rowp2 = (T == 2) ? tab2 + tab_base(m, Lb) : rowp;
     const float fm2 = (float)(m * m);
     float2 P1[C], P2[C];
     // row sums: Re z1 + Re z2, Im z1, Im z2, n Im z1, n Im z2, and the beta-derivative part
-    float rS[C], rI1[C], rI2[C], rN1[C], rN2[C], rB[C];
+    float rS[CT], rI1[CT], rI2[CT], rN1[CT], rN2[CT], rB[CT];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       P1[j] = cmul(Uq[j], Wrow[j]);
       P2[j] = cmul(Uq[j], cconj(Wrow[j]));
-      rS[j] = rI1[j] = rI2[j] = rN1[j] = rN2[j] = rB[j] = 0.f;
     }
+#pragma unroll
+    for (int i = 0; i < CT; ++i) rS[i] = rI1[i] = rI2[i] = rN1[i] = rN2[i] = rB[i] = 0.f;
     for (int n = qg - m; n <= m; n += G) {
       const float lb = __ldg(lbin + m * kBinStride + m + n);
       const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n;
       const bool odd = (m - n) & 1;
       float e1[C], e2[C], p1[C], p2[C];
-      float a1r[C], a1i[C], a2r[C], a2i[C], b1r[C], b1i[C], b2r[C], b2i[C];
+      float a1r[CT], a1i[CT], a2r[CT], a2i[CT], b1r[CT], b1i[CT], b2r[CT], b2i[CT];
       const float4* ep = rowp + (n + m);
-      float4 xv = *ep;
+      const float4* ep2 = rowp2 + (n + m);
+      float4 xv[T];
+      xv[0] = *ep;
+      if (T == 2) xv[T - 1] = *ep2;
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         float d = exp2f(lb + fa * lcc[j] + fd * lss[j]);
         d = odd ? -d : d;
         const float dp = 0.5f * d * (fd * rcs[j] - fa * rsc[j]);
-        a1r[j] = d * xv.x; a1i[j] = d * xv.y; a2r[j] = d * xv.z; a2i[j] = d * xv.w;
-        b1r[j] = dp * xv.x; b1i[j] = dp * xv.y; b2r[j] = dp * xv.z; b2i[j] = dp * xv.w;
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          const int i = j * T + k;
+          a1r[i] = d * xv[k].x; a1i[i] = d * xv[k].y; a2r[i] = d * xv[k].z; a2i[i] = d * xv[k].w;
+          b1r[i] = dp * xv[k].x; b1i[i] = dp * xv[k].y; b2r[i] = dp * xv[k].z; b2i[i] = dp * xv[k].w;
+        }
         e1[j] = d; e2[j] = 0.f; p1[j] = dp; p2[j] = 0.f;
       }
       const float mn = (float)(m * n), fn2 = (float)(n * n);
-      // one step of band l for start j: (E1, E2, P1, P2) -> (EN, PN), accumulate against X
-#define BH_STEP(J, EN, PN, E1, E2, P1, P2, K, G_, X)                                \
-  {                                                                               \
-    const float t_ = fmaf(-mn, (K).x, xb[J]);                                     \
-    EN = fmaf(t_, E1, -(G_) * E2);                                                \
-    PN = fmaf(t_, P1, -fmaf(sinb[J], E1, (G_) * P2));                             \
-    a1r[J] = fmaf(EN, (X).x, a1r[J]); a1i[J] = fmaf(EN, (X).y, a1i[J]);           \
-    a2r[J] = fmaf(EN, (X).z, a2r[J]); a2i[J] = fmaf(EN, (X).w, a2i[J]);           \
-    b1r[J] = fmaf(PN, (X).x, b1r[J]); b1i[J] = fmaf(PN, (X).y, b1i[J]);           \
-    b2r[J] = fmaf(PN, (X).z, b2r[J]); b2i[J] = fmaf(PN, (X).w, b2i[J]);           \
+      // one step of band l for start j: (E1, E2, P1, P2) -> (EN, PN), accumulated against every table's X
+#define BH_STEP(J, EN, PN, E1, E2, P1, P2, K, G_, X)                                 \
+  {                                                                                \
+    const float t_ = fmaf(-mn, (K).x, xb[J]);                                      \
+    EN = fmaf(t_, E1, -(G_) * E2);                                                 \
+    PN = fmaf(t_, P1, -fmaf(sinb[J], E1, (G_) * P2));                              \
+    _Pragma("unroll") for (int k_ = 0; k_ < T; ++k_) {                             \
+      const int i_ = (J) * T + k_;                                                 \
+      a1r[i_] = fmaf(EN, (X)[k_].x, a1r[i_]); a1i[i_] = fmaf(EN, (X)[k_].y, a1i[i_]); \
+      a2r[i_] = fmaf(EN, (X)[k_].z, a2r[i_]); a2i[i_] = fmaf(EN, (X)[k_].w, a2i[i_]); \
+      b1r[i_] = fmaf(PN, (X)[k_].x, b1r[i_]); b1i[i_] = fmaf(PN, (X)[k_].y, b1i[i_]); \
+      b2r[i_] = fmaf(PN, (X)[k_].z, b2r[i_]); b2i[i_] = fmaf(PN, (X)[k_].w, b2i[i_]); \
+    }                                                                              \
   }
       int l = m + 1;
       for (; l + 1 <= L; l += 2) {  // two bands per iteration: no register rotation, half the loop overhead
         const float4 k0 = c_ecoef[l], k1 = c_ecoef[l + 1];
-        const float4 x0 = ep[w], x1 = ep[2 * w];
+        float4 x0[T], x1[T];
+        x0[0] = ep[w];
+        x1[0] = ep[2 * w];
+        if (T == 2) {
+          x0[T - 1] = ep2[w];
+          x1[T - 1] = ep2[2 * w];
+          ep2 += 2 * w;
+        }
         ep += 2 * w;
         const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
         const float g1 = (k1.z - fm2) * (k1.z - fn2) * k1.y;
@@ -265,7 +289,9 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
       }
       if (l <= L) {
         const float4 k0 = c_ecoef[l];
-        const float4 x0 = ep[w];
+        float4 x0[T];
+        x0[0] = ep[w];
+        if (T == 2) x0[T - 1] = ep2[w];
         const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
@@ -276,14 +302,18 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
 #undef BH_STEP
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        const float z1r = P1[j].x * a1r[j] - P1[j].y * a1i[j], z1i = P1[j].x * a1i[j] + P1[j].y * a1r[j];
-        const float z2r = P2[j].x * a2r[j] - P2[j].y * a2i[j], z2i = P2[j].x * a2i[j] + P2[j].y * a2r[j];
-        rS[j] += z1r + z2r;
-        rI1[j] += z1i;
-        rI2[j] += z2i;
-        rN1[j] = fmaf(fn, z1i, rN1[j]);
-        rN2[j] = fmaf(fn, z2i, rN2[j]);
-        rB[j] += (P1[j].x * b1r[j] - P1[j].y * b1i[j]) + (P2[j].x * b2r[j] - P2[j].y * b2i[j]);
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          const int i = j * T + k;
+          const float z1r = P1[j].x * a1r[i] - P1[j].y * a1i[i], z1i = P1[j].x * a1i[i] + P1[j].y * a1r[i];
+          const float z2r = P2[j].x * a2r[i] - P2[j].y * a2i[i], z2i = P2[j].x * a2i[i] + P2[j].y * a2r[i];
+          rS[i] += z1r + z2r;
+          rI1[i] += z1i;
+          rI2[i] += z2i;
+          rN1[i] = fmaf(fn, z1i, rN1[i]);
+          rN2[i] = fmaf(fn, z2i, rN2[i]);
+          rB[i] += (P1[j].x * b1r[i] - P1[j].y * b1i[i]) + (P2[j].x * b2r[i] - P2[j].y * b2i[i]);
+        }
         P1[j] = cmul(P1[j], R1[j]);
         P2[j] = cmul(P2[j], R2[j]);
       }
@@ -291,28 +321,36 @@ __device__ void eval_rotations(const float4* __restrict__ tab, int Lb, int L, co
     const float fm = (float)m;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      S[j] += rS[j];
-      Sa[j] += fm * rI1[j] + rN2[j];
-      Sg[j] += rN1[j] + fm * rI2[j];
-      Sb[j] += rB[j];
+#pragma unroll
+      for (int k = 0; k < T; ++k) {
+        const int i = j * T + k;
+        S[i] += rS[i];
+        Sa[i] += fm * rI1[i] + rN2[i];
+        Sg[i] += rN1[i] + fm * rI2[i];
+        Sb[i] += rB[i];
+      }
       Wrow[j] = cmul(Wrow[j], Ed2[j]);
     }
   }
 #pragma unroll
   for (int j = 0; j < C; ++j) {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) {
-      S[j] += __shfl_xor_sync(0xffffffffu, S[j], o);
-      Sa[j] += __shfl_xor_sync(0xffffffffu, Sa[j], o);
-      Sb[j] += __shfl_xor_sync(0xffffffffu, Sb[j], o);
-      Sg[j] += __shfl_xor_sync(0xffffffffu, Sg[j], o);
-    }
     const float2 eg = cmul(es[j], cconj(ed[j]));
-    const float Q = (sinb[j] > 1e-30f) ? (xb[j] * Sg[j] - Sa[j]) / sinb[j] : 0.f;
-    out[j].S = S[j];
-    out[j].gx = Sb[j] * eg.y + Q * eg.x;
-    out[j].gy = Sb[j] * eg.x - Q * eg.y;
-    out[j].gz = Sg[j];
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      const int i = j * T + k;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        S[i] += __shfl_xor_sync(0xffffffffu, S[i], o);
+        Sa[i] += __shfl_xor_sync(0xffffffffu, Sa[i], o);
+        Sb[i] += __shfl_xor_sync(0xffffffffu, Sb[i], o);
+        Sg[i] += __shfl_xor_sync(0xffffffffu, Sg[i], o);
+      }
+      const float Q = (sinb[j] > 1e-30f) ? (xb[j] * Sg[i] - Sa[i]) / sinb[j] : 0.f;
+      out[i].S = S[i];
+      out[i].gx = Sb[i] * eg.y + Q * eg.x;
+      out[i].gy = Sb[i] * eg.x - Q * eg.y;
+      out[i].gz = Sg[i];
+    }
   }
 }
 
@@ -321,7 +359,7 @@ __device__ __forceinline__ Eval eval_one(const float4* __restrict__ tab, int Lb,
                                          const float* __restrict__ lbin) {
   const float4 qq[1] = {q};
   Eval e[1];
-  eval_rotations<G, 1>(tab, Lb, L, qq, qg, lbin, e);
+  eval_rotations<G, 1>(tab, nullptr, Lb, L, qq, qg, lbin, e);
   return e[0];
 }
 
@@ -806,6 +844,17 @@ __device__ __forceinline__ Eval constrained(const Eval& s, const Eval& d) {
   return c;
 }
 
+// C(R) and its gradient from one pass over the orbits that scores R against the subtomogram's table and
+// the wedge norm's table together.
+template <int G>
+__device__ __forceinline__ Eval eval_constrained(const float4* __restrict__ tab, const float4* __restrict__ tabw, int Lb,
+                                                 int L, float4 q, int qg, const float* __restrict__ lbin) {
+  const float4 qq[1] = {q};
+  Eval e[2];
+  eval_rotations<G, 1, 2>(tab, tabw, Lb, L, qq, qg, lbin, e);
+  return constrained(e[0], e[1]);
+}
+
 template <int G, int NT>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_wedge(const AlignArgs a, const Layout wlay,
                                                                     const float2* __restrict__ wt,
@@ -828,7 +877,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_wedge(const AlignA
     const int L = a.stages[st];
     const float hmax = 3.14159265358979f / (float)L;
     float h = 0.5f * hmax;
-    cur = constrained(eval_one<G>(smem_tab, a.Lb, L, q, qg, a.lbin), eval_one<G>(tabw, a.Lb, L, q, qg, a.lbin));
+    cur = eval_constrained<G>(smem_tab, tabw, a.Lb, L, q, qg, a.lbin);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -837,8 +886,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_wedge(const AlignA
       sincosf(stop ? 0.f : 0.5f * h, &sh, &ch);
       const float4 dq = make_float4(ch, sh * cur.gx * inv, sh * cur.gy * inv, sh * cur.gz * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const Eval tr = constrained(eval_one<G>(smem_tab, a.Lb, L, qt, qg, a.lbin),
-                                  eval_one<G>(tabw, a.Lb, L, qt, qg, a.lbin));
+      const Eval tr = eval_constrained<G>(smem_tab, tabw, a.Lb, L, qt, qg, a.lbin);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -894,7 +942,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs 
     const float hmax = 3.14159265358979f / (float)L;
 #pragma unroll
     for (int j = 0; j < C; ++j) h[j] = 0.5f * hmax;
-    eval_rotations<G, C>(smem_tab, a.Lb, L, q, qg, a.lbin, cur);
+    eval_rotations<G, C>(smem_tab, nullptr, a.Lb, L, q, qg, a.lbin, cur);
     for (int t = 0; t < a.steps; ++t) {
       float4 qt[C];
       bool stop[C];
@@ -909,7 +957,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs 
         qt[j] = qnormalize(qmul(q[j], dq));
       }
       Eval tr[C];
-      eval_rotations<G, C>(smem_tab, a.Lb, L, qt, qg, a.lbin, tr);
+      eval_rotations<G, C>(smem_tab, nullptr, a.Lb, L, qt, qg, a.lbin, tr);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         if (!stop[j]) {
@@ -1365,8 +1413,8 @@ int launch_refine(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStream
 
 // Default lanes per start (before autotuning): about 512 resident threads per SM, given how many orbit
 // tables of band Lb fit in an SM's 227 KB of shared memory (at most 8 CTAs).
-int default_group(int S, int Lb) {
-  const int ctas = std::max(1, std::min(8, (int)(232448 / std::max<size_t>(1, table_bytes(Lb)))));
+int default_group(int S, int Lb, int tables = 1) {
+  const int ctas = std::max(1, std::min(8, (int)(232448 / std::max<size_t>(1, tables * table_bytes(Lb)))));
   const int want = std::max(32, 512 / ctas);
   int G = 1;
   while (G < 16 && S * G < want && round_up(S * G * 2, 32) <= kMaxThreads) G *= 2;
@@ -1558,7 +1606,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     if (opts->tmpl_index) return fail(BH_ERR_ARG, "the constrained ascent takes one template");
     if (w->L < a.Lb) return fail(BH_ERR_ARG, "wedge prepared to band %d, stages reach %d", w->L, a.Lb);
     if (w->layout.Lmax != p->Lmax) return fail(BH_ERR_ARG, "wedge prepared for another plan");
-    if (opts->group == 0) G = default_group(S, a.Lb);
+    if (opts->group == 0) G = default_group(S, a.Lb, 2);  // two orbit tables per CTA
     if (round_up(S * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
     st = launch_wedge(a, w, G, static_cast<cudaStream_t>(stream));
