@@ -406,7 +406,7 @@ def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
                        "candidate_band": w.stages[0], "candidates": S, "newton_steps_per_band": args.sec3_steps,
                        "bands": w.stages, "fp64_rescore_top_k": min(args.refine, S),
                        "newton_lanes_per_start": tune["newton_group"] if tune else "default"},
-            "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 2 + (1 if min(args.refine, S) else 0)}
+            "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 3 + 1 + (1 if min(args.refine, S) else 0)}
 
 
 def wedge_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:

@@ -287,14 +287,17 @@ int bh_grid_info(const bh_grid* grid, int* n, int* max_neighbors, long long* n_e
 int bh_grid_neighbors(const bh_grid* grid, int* offsets, int* neighbors, long long cap);
 
 /*
- * Candidate starts for B subtomograms, one launch.  For each subtomogram: Eq. 2 truncated at band L
- * at every grid rotation (FP32, the alignment's evaluation); grid point i ranks above j when its
- * score is larger, or equal with i < j; i is a local maximum when it ranks above all of its
- * neighbours.  The candidates are the local maxima in rank order followed, if there are fewer than
- * S, by the other grid points in rank order; the first S are written.
- *   L               band, 1..Lmax (the lowest marching band; the grid scores' orbit table of band L and
- *                   the sort keys share one CTA's shared memory: 16-byte table entries plus 8 bytes
- *                   per grid point rounded up to a power of two, at most 227 KB)
+ * Candidate starts for B subtomograms.  For each subtomogram: Eq. 2 truncated at band L at every
+ * grid rotation (FP32; the grid rotations are shared by all subtomograms, so their Wigner factors are
+ * computed once per grid and band and the B x n scores are one dense contraction with the
+ * subtomograms' orbit tables); grid point i ranks above j when its score is larger, or equal with
+ * i < j; i is a local maximum when it ranks above all of its neighbours.  The candidates are the local
+ * maxima in rank order followed, if there are fewer than S, by the other grid points in rank order;
+ * the first S are written.  The first call for a band builds that band's factors for the grid
+ * (synchronously, on a private stream); work memory (B x n scores) comes from stream-ordered
+ * allocation on `stream`.
+ *   L               band, 1..Lmax (the lowest marching band; one CTA's shared memory holds 8 bytes of
+ *                   sort key per grid point -- per power of two above n when S > 64 -- at most 227 KB)
  *   tmpl, sub, tmpl_index, n_templates   as bh_align_batch
  *   S               1..n candidates per subtomogram
  *   starts_out      device, B * S * 4 floats: the candidate rotations (grid entries as given), ready

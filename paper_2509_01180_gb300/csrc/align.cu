@@ -1929,6 +1929,8 @@ struct bh_grid {
   float4* d_q = nullptr;   // [n] rotations (w, x, y, z) as given
   int* d_off = nullptr;    // [n + 1] CSR offsets of the neighbour lists
   int* d_nbr = nullptr;    // [n_edges] neighbour indices, ascending per grid point
+  mutable std::mutex mu;
+  mutable std::map<int, float4*> coef;  // band L -> [n_pad][Kf4(L)] Wigner coefficients of every rotation
 };
 
 namespace bh {
@@ -1984,49 +1986,100 @@ struct GridArgs {
   const int* off;
   const int* nbr;
   int L;
-  float4* starts_out;  // [B][S]
-  int* index_out;      // [B][S] or NULL
-  float* score_out;    // [B][n] or NULL
+  float4* starts_out;   // [B][S]
+  int* index_out;       // [B][S] or NULL
+  float* score_out;     // [B][n] or NULL
+  const float* scores;  // [B_pad][ld] band-L scores of every grid rotation
+  int ld;
 };
 
 constexpr int kSelectRounds = 64;  // up to this many candidates: S rounds of a block-wide argmax; above: sort
 
-// One CTA per subtomogram: Eq. 2 at band L on every grid rotation (orbit table of band L in shared memory),
-// local-maximum flags from the neighbour lists, then the S highest keys, either by S rounds of a block-wide
-// argmax (S <= kSelectRounds) or by a bitonic sort of next_pow2(n) keys.
-template <int C>
-__global__ void __launch_bounds__(kCandThreads, 3) k_grid_candidates(const AlignArgs a, const GridArgs g) {
-  extern __shared__ float4 smem_tab[];
+// Orbit-table entries of band L padded to a multiple of 4 float4 (the GEMM's K multiple of 16 floats).
+__host__ __device__ inline int cand_kf4(int L) { return (tab_base(L + 1, L) + 3) & ~3; }
+
+// Row p < B: the orbit table of band L of subtomogram p (the score's left factor, flattened); padding
+// entries and rows p >= B are zero.
+__global__ void __launch_bounds__(128) k_cand_tables(const AlignArgs a, int L, int Kf4, float4* __restrict__ X) {
+  const int p = blockIdx.x;
+  float4* row = X + (size_t)p * Kf4;
+  const int nent = p < a.B ? tab_base(L + 1, L) : 0;
+  if (p < a.B)
+    build_table(row, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, L, threadIdx.x, blockDim.x);
+  for (int e = nent + threadIdx.x; e < Kf4; e += blockDim.x) row[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Wigner coefficients of the grid rotations at band L: for rotation i and orbit-table entry (m, l, n) the
+// factor e_l (Re P1, -Im P1, Re P2, -Im P2) that eval_scores multiplies that entry by, so that the band-L
+// score of a subtomogram is the dot product of its orbit table with row i -- a dense contraction over
+// all subtomograms and grid rotations.  One thread per rotation, the recursion and phases of eval_scores.
+__global__ void __launch_bounds__(128) k_grid_coef(const float4* __restrict__ gq, int n, int n_pad, int L, int Kf4,
+                                                   const float* __restrict__ lbin, float4* __restrict__ coef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;
+  float4* out = coef + (size_t)i * Kf4;
+  if (i >= n) {
+    for (int e = 0; e < Kf4; ++e) out[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float4 q = qnormalize(gq[i]);
+  const float w = q.x, x = q.y, y = q.z, z = q.w;
+  const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+  const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+  const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+  const float xb = (cb - sb) * (cb + sb);
+  const float lcc = log2f(fmaxf(cb, 1e-30f)), lss = log2f(fmaxf(sb, 1e-30f));
+  const float2 Es = cconj(es);
+  const float2 R1 = cmul(Es, ed), R2 = cmul(Es, cconj(ed));
+  const float2 Ed = cconj(ed);
+  const float2 Ed2 = cmul(Ed, Ed);
+  float2 Wrow = make_float2(1.f, 0.f);
+  for (int m = 0; m <= L; ++m) {
+    const int wd = 2 * m + 1;
+    float4* rowp = out + tab_base(m, L);
+    const float fm2 = (float)(m * m);
+    float2 P1 = Wrow, P2 = cconj(Wrow);
+    for (int nn = -m; nn <= m; ++nn) {
+      const float lb = __ldg(lbin + m * kBinStride + m + nn);
+      float d = exp2f(lb + (float)(m + nn) * lcc + (float)(m - nn) * lss);
+      d = ((m - nn) & 1) ? -d : d;
+      float4* ep = rowp + (nn + m);
+      *ep = make_float4(d * P1.x, -d * P1.y, d * P2.x, -d * P2.y);
+      const float mn = (float)(m * nn), fn2 = (float)(nn * nn);
+      float e1 = d, e2 = 0.f;
+      for (int l = m + 1; l <= L; ++l) {
+        const float4 k0 = c_ecoef[l];
+        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
+        const float en = fmaf(fmaf(-mn, k0.x, xb), e1, -g0 * e2);
+        ep += wd;
+        *ep = make_float4(en * P1.x, -en * P1.y, en * P2.x, -en * P2.y);
+        e2 = e1;
+        e1 = en;
+      }
+      P1 = cmul(P1, R1);
+      P2 = cmul(P2, R2);
+    }
+    Wrow = cmul(Wrow, Ed2);
+  }
+  for (int e = tab_base(L + 1, L); e < Kf4; ++e) out[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// One CTA per subtomogram: the band-L scores of every grid rotation (precomputed by the contraction) as
+// rank keys in shared memory, local-maximum flags from the neighbour lists, then the S highest keys,
+// either by S rounds of a block-wide argmax (S <= kSelectRounds) or by a bitonic sort of next_pow2(n)
+// keys.
+__global__ void __launch_bounds__(kCandThreads, 4) k_grid_candidates(const AlignArgs a, const GridArgs g) {
+  extern __shared__ unsigned long long key[];
   __shared__ unsigned long long wbest[kCandThreads / 32];
   const int p = blockIdx.x;
-  const int ntab = tab_base(a.Lb + 1, a.Lb);
   const bool sort = a.S > kSelectRounds;
   const int nkeys = sort ? g.npow2 : g.n;
-  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_tab + ntab);
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
-              blockDim.x);
   for (int i = g.n + threadIdx.x; i < nkeys; i += blockDim.x) key[i] = 0ull;  // padding ranks last
-  __syncthreads();
-  // one lane per grid rotation, C rotations per thread and pass
-  const int per_pass = blockDim.x * C;
-  const int passes = (g.n + per_pass - 1) / per_pass;
-  for (int it = 0; it < passes; ++it) {
-    float4 q[C];
-    int idx[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      idx[j] = it * per_pass + j * blockDim.x + threadIdx.x;
-      q[j] = qnormalize(g.q[idx[j] < g.n ? idx[j] : g.n - 1]);
-    }
-    float e[C];
-    eval_scores<C>(smem_tab, a.Lb, g.L, q, a.lbin, e);
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      if (idx[j] < g.n) {
-        key[idx[j]] = grid_key(e[j], idx[j]);
-        if (g.score_out) g.score_out[(size_t)p * g.n + idx[j]] = e[j];
-      }
-    }
+  const float* srow = g.scores + (size_t)p * g.ld;
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
+    const float e = srow[i];
+    key[i] = grid_key(e, i);
+    if (g.score_out) g.score_out[(size_t)p * g.n + i] = e;
   }
   __syncthreads();
   // local maxima: thread t owns grid points t + k * blockDim (k < n / blockDim <= 64), flags in a bit mask
@@ -2101,9 +2154,7 @@ __global__ void __launch_bounds__(kCandThreads, 3) k_grid_candidates(const Align
   }
 }
 
-size_t grid_smem(int L, int n, int npow2, int S) {
-  return table_bytes(L) + (size_t)(S > kSelectRounds ? npow2 : n) * 8;
-}
+size_t grid_smem(int n, int npow2, int S) { return (size_t)(S > kSelectRounds ? npow2 : n) * 8; }
 }  // namespace
 }  // namespace bh
 
@@ -2155,6 +2206,7 @@ extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double r
 
 extern "C" int bh_grid_destroy(bh_grid* g) {
   if (!g) return BH_OK;
+  for (auto& kv : g->coef) cudaFree(kv.second);
   cudaFree(g->d_q);
   cudaFree(g->d_off);
   cudaFree(g->d_nbr);
@@ -2197,8 +2249,8 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
   int dev = 0;
   BH_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != grid->device) return fail(BH_ERR_ARG, "grid lives on device %d, current device is %d", grid->device, dev);
-  const size_t smem = grid_smem(L, grid->n, grid->npow2, S);
-  if (smem > 232448) return fail(BH_ERR_ARG, "band %d with %d grid points needs %zu bytes of shared memory", L, grid->n, smem);
+  const size_t smem = grid_smem(grid->n, grid->npow2, S);
+  if (smem > 232448) return fail(BH_ERR_ARG, "%d grid points need %zu bytes of shared memory", grid->n, smem);
   AlignArgs a{};
   a.lay = p->layout;
   a.tmpl = reinterpret_cast<const float2*>(tmpl);
@@ -2210,12 +2262,60 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
   a.Lb = L;
   a.P = p->d_P;
   a.lbin = p->d_lbin;
-  GridArgs g{grid->d_q, grid->n, grid->npow2, grid->d_off, grid->d_nbr, L,
-             reinterpret_cast<float4*>(starts_out), index_out, grid_score_out};
-  static std::atomic<int> have{0};
-  int st = ensure_smem(k_grid_candidates<2>, have, smem);
-  if (st != BH_OK) return st;
-  k_grid_candidates<2><<<B, kCandThreads, smem, static_cast<cudaStream_t>(stream)>>>(a, g);
-  BH_CHECK_LAUNCH();
-  return BH_OK;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const int Kf4 = cand_kf4(L), n_pad = round_up(grid->n, 128), B_pad = round_up(B, 128);
+  // Wigner coefficients of the grid at band L: built once per (grid, band), on a private stream that is
+  // synchronised before use, so that every caller stream sees the finished matrix
+  float4* coef = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(grid->mu);
+    auto it = grid->coef.find(L);
+    if (it != grid->coef.end()) {
+      coef = it->second;
+    } else {
+      BH_CUDA_TRY(cudaMalloc(&coef, (size_t)n_pad * Kf4 * sizeof(float4)));
+      cudaStream_t s2 = nullptr;
+      cudaError_t e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+      if (e == cudaSuccess) {
+        k_grid_coef<<<(n_pad + 127) / 128, 128, 0, s2>>>(grid->d_q, grid->n, n_pad, L, Kf4, p->d_lbin, coef);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s2);
+        cudaStreamDestroy(s2);
+      }
+      if (e != cudaSuccess) {
+        cudaFree(coef);
+        return fail(BH_ERR_CUDA, "grid coefficients for band %d: %s", L, cudaGetErrorString(e));
+      }
+      grid->coef[L] = coef;
+    }
+  }
+  // band-L scores of every (subtomogram, grid rotation): orbit tables [B_pad][4 Kf4] times coefficients
+  // [n_pad][4 Kf4]^T, one FP32 GEMM
+  float4* X = nullptr;
+  float* scores = nullptr;
+  BH_CUDA_TRY(cudaMallocAsync(&X, (size_t)B_pad * Kf4 * sizeof(float4), cs));
+  cudaError_t ea = cudaMallocAsync(&scores, (size_t)B_pad * n_pad * sizeof(float), cs);
+  if (ea != cudaSuccess) {
+    cudaFreeAsync(X, cs);
+    return fail(ea == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA, "candidate scores: %s", cudaGetErrorString(ea));
+  }
+  k_cand_tables<<<B_pad, 128, 0, cs>>>(a, L, Kf4, X);
+  int st = BH_OK;
+  cudaError_t el = cudaGetLastError();
+  if (el != cudaSuccess) st = fail(BH_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(el));
+  if (st == BH_OK) st = sgemm_nt(reinterpret_cast<const float*>(X), reinterpret_cast<const float*>(coef), scores, B_pad, n_pad, 4 * Kf4, cs);
+  if (st == BH_OK) {
+    GridArgs g{grid->d_q, grid->n, grid->npow2, grid->d_off, grid->d_nbr, L,
+               reinterpret_cast<float4*>(starts_out), index_out, grid_score_out, scores, n_pad};
+    static std::atomic<int> have{0};
+    st = ensure_smem(k_grid_candidates, have, smem);
+    if (st == BH_OK) {
+      k_grid_candidates<<<B, kCandThreads, smem, cs>>>(a, g);
+      el = cudaGetLastError();
+      if (el != cudaSuccess) st = fail(BH_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(el));
+    }
+  }
+  cudaFreeAsync(X, cs);
+  cudaFreeAsync(scores, cs);
+  return st;
 }

@@ -112,6 +112,8 @@ int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, i
 // addresses) is given.
 int expand_into(bh_plan* p, const float* vols, const float* const* vptr, int B, float* coeffs, void* scratch_x,
                 float* scratch_c, int rows_cap, cudaStream_t stream);
+// C[M][N] = A[M][K] B[N][K]^T, FP32 (M, N multiples of 128, K of 16)
+int sgemm_nt(const float* A, const float* B, float* C, int M, int N, int K, cudaStream_t stream);
 // align.cu
 int align_init_constants();
 }  // namespace bh

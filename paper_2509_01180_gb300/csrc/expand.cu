@@ -220,6 +220,18 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, c
   }
 }
 
+}  // namespace
+
+// C[M][N] = A[M][K] B[N][K]^T in FP32 on the caller's stream (M, N multiples of 128, K of 16).
+int sgemm_nt(const float* A, const float* Bm, float* C, int M, int N, int K, cudaStream_t stream) {
+  if (M % SG_BM || N % SG_BN || K % SG_BK || M <= 0 || N <= 0 || K <= 0)
+    return fail(BH_ERR_ARG, "sgemm_nt: M=%d N=%d K=%d not tile multiples", M, N, K);
+  k_sgemm_nt<<<dim3(M / SG_BM, N / SG_BN, 1), 256, 0, stream>>>(A, Bm, C, M, N, K, K, 0);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+namespace {
 // ---------------------------------------------------------------- tcgen05 / TMA / mbarrier primitives
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
