@@ -1929,6 +1929,8 @@ struct bh_grid {
   float4* d_q = nullptr;   // [n] rotations (w, x, y, z) as given
   int* d_off = nullptr;    // [n + 1] CSR offsets of the neighbour lists
   int* d_nbr = nullptr;    // [n_edges] neighbour indices, ascending per grid point
+  unsigned* d_pairs = nullptr;  // [n_edges / 2] neighbour pairs i < j packed as (i << 14) | j
+  int n_pairs = 0;
   mutable std::mutex mu;
   mutable std::map<int, float4*> coef;  // band L -> [n_pad][Kf4(L)] Wigner coefficients of every rotation
 };
@@ -1936,6 +1938,7 @@ struct bh_grid {
 namespace bh {
 namespace {
 constexpr int kGridMax = 16384;  // the sort keys of one subtomogram's grid scores live in shared memory
+static_assert(kGridMax <= (1 << 14), "neighbour pairs pack two 14-bit grid indices");
 constexpr int kCandThreads = 256;
 
 // |q_i . q_j| >= c, the dot product summed in the order w, x, y, z in FP64 (exact products of floats).  An
@@ -1991,6 +1994,8 @@ struct GridArgs {
   float* score_out;     // [B][n] or NULL
   const float* scores;  // [B_pad][ld] band-L scores of every grid rotation
   int ld;
+  const unsigned* pairs;  // neighbour pairs (i << 14) | j, i < j
+  int npairs;
 };
 
 constexpr int kSelectRounds = 64;  // up to this many candidates: S rounds of a block-wide argmax; above: sort
@@ -2082,17 +2087,19 @@ __global__ void __launch_bounds__(kCandThreads, 4) k_grid_candidates(const Align
     if (g.score_out) g.score_out[(size_t)p * g.n + i] = e;
   }
   __syncthreads();
-  // local maxima: thread t owns grid points t + k * blockDim (k < n / blockDim <= 64), flags in a bit mask
-  unsigned long long fmask = 0ull;
-  for (int i = threadIdx.x, k = 0; i < g.n; i += blockDim.x, ++k) {
-    const unsigned long long ki = key[i];
-    bool mx = true;
-    for (int e = g.off[i], e1 = g.off[i + 1]; e < e1 && mx; ++e) mx = key[g.nbr[e]] < ki;
-    if (mx) fmask |= 1ull << k;
+  // local maxima over the neighbour pairs (coalesced 4-byte loads, each pair once): of every pair the
+  // lower-ranked point is not a maximum
+  unsigned char* notmax = reinterpret_cast<unsigned char*>(key + nkeys);
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x) notmax[i] = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < g.npairs; e += blockDim.x) {
+    const unsigned w = __ldg(g.pairs + e);
+    const int i = (int)(w >> 14), j = (int)(w & 0x3FFFu);
+    notmax[key[i] > key[j] ? j : i] = 1;
   }
   __syncthreads();
-  for (int i = threadIdx.x, k = 0; i < g.n; i += blockDim.x, ++k)
-    if ((fmask >> k) & 1ull) key[i] |= 1ull << 63;
+  for (int i = threadIdx.x; i < g.n; i += blockDim.x)
+    if (!notmax[i]) key[i] |= 1ull << 63;
   __syncthreads();
   if (!sort) {
     unsigned long long mine = 0ull;
@@ -2154,7 +2161,9 @@ __global__ void __launch_bounds__(kCandThreads, 4) k_grid_candidates(const Align
   }
 }
 
-size_t grid_smem(int n, int npow2, int S) { return (size_t)(S > kSelectRounds ? npow2 : n) * 8; }
+size_t grid_smem(int n, int npow2, int S) {
+  return (size_t)(S > kSelectRounds ? npow2 : n) * 8 + (size_t)round_up(n, 16);  // rank keys + local-max flags
+}
 }  // namespace
 }  // namespace bh
 
@@ -2200,6 +2209,19 @@ extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double r
   k_grid_nbr<<<nbr_blocks, 256>>>(g->d_q, n, c, g->d_off, g->d_nbr);
   BH_CHECK_LAUNCH();
   BH_CUDA_TRY(cudaDeviceSynchronize());
+  // each neighbour pair once (the relation is symmetric: the same FP64 dot product either way)
+  std::vector<int> nbr((size_t)g->n_edges);
+  if (g->n_edges)
+    BH_CUDA_TRY(cudaMemcpy(nbr.data(), g->d_nbr, (size_t)g->n_edges * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<unsigned> pairs;
+  pairs.reserve((size_t)g->n_edges / 2 + 1);
+  for (int i = 0; i < n; ++i)
+    for (int e = off[i]; e < off[i + 1]; ++e)
+      if (nbr[e] > i) pairs.push_back(((unsigned)i << 14) | (unsigned)nbr[e]);
+  g->n_pairs = (int)pairs.size();
+  BH_CUDA_TRY(cudaMalloc(&g->d_pairs, std::max<size_t>(1, pairs.size()) * sizeof(unsigned)));
+  if (!pairs.empty())
+    BH_CUDA_TRY(cudaMemcpy(g->d_pairs, pairs.data(), pairs.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
   *out = g.release();
   return BH_OK;
 }
@@ -2207,6 +2229,7 @@ extern "C" int bh_grid_create(bh_grid** out, const float* quats, int n, double r
 extern "C" int bh_grid_destroy(bh_grid* g) {
   if (!g) return BH_OK;
   for (auto& kv : g->coef) cudaFree(kv.second);
+  cudaFree(g->d_pairs);
   cudaFree(g->d_q);
   cudaFree(g->d_off);
   cudaFree(g->d_nbr);
@@ -2306,7 +2329,8 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
   if (st == BH_OK) st = sgemm_nt(reinterpret_cast<const float*>(X), reinterpret_cast<const float*>(coef), scores, B_pad, n_pad, 4 * Kf4, cs);
   if (st == BH_OK) {
     GridArgs g{grid->d_q, grid->n, grid->npow2, grid->d_off, grid->d_nbr, L,
-               reinterpret_cast<float4*>(starts_out), index_out, grid_score_out, scores, n_pad};
+               reinterpret_cast<float4*>(starts_out), index_out, grid_score_out, scores, n_pad,
+               grid->d_pairs, grid->n_pairs};
     static std::atomic<int> have{0};
     st = ensure_smem(k_grid_candidates, have, smem);
     if (st == BH_OK) {
