@@ -583,7 +583,9 @@ def main():
     ap.add_argument("--count", type=int, default=None, help="subtomograms per GPU (default: the workload's)")
     ap.add_argument("--form", choices=["both", "bf16split", "fp32"], default="both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="serving leg duration, the 60 s window of the serving workload (0 = skip)")
+    ap.add_argument("--serve-newton-seconds", type=float, default=20.0, help="duration of the Newton serving leg")
     ap.add_argument("--mixed-scale", type=float, default=1.0, help="class-count multiplier of the mixed workload")
     ap.add_argument("--no-autotune", action="store_true", help="use --group/--starts-per-thread instead of tuning")
     ap.add_argument("--group", type=int, default=4, help="lanes per start (group) with --no-autotune")
@@ -731,7 +733,7 @@ def main():
         if world == 1 and args.serve_seconds > 0:
             line["serving"] = serving_leg(args.serve_seconds)
             if args.serve_newton:
-                line["serving_newton"] = serving_leg(args.serve_seconds, newton=True)
+                line["serving_newton"] = serving_leg(args.serve_newton_seconds, newton=True)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

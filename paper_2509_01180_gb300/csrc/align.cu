@@ -2080,11 +2080,25 @@ __global__ void __launch_bounds__(kCandThreads, 4) k_grid_candidates(const Align
   const bool sort = a.S > kSelectRounds;
   const int nkeys = sort ? g.npow2 : g.n;
   for (int i = g.n + threadIdx.x; i < nkeys; i += blockDim.x) key[i] = 0ull;  // padding ranks last
+  // global loads in batches of kBatch per thread (coalesced across the block), so that a thread waits
+  // about one L2 latency per batch rather than per element
+  constexpr int kBatch = 8;
   const float* srow = g.scores + (size_t)p * g.ld;
-  for (int i = threadIdx.x; i < g.n; i += blockDim.x) {
-    const float e = srow[i];
-    key[i] = grid_key(e, i);
-    if (g.score_out) g.score_out[(size_t)p * g.n + i] = e;
+  for (int i0 = threadIdx.x; i0 < g.n; i0 += kBatch * blockDim.x) {
+    float e[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * blockDim.x;
+      e[u] = i < g.n ? __ldg(srow + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < g.n) {
+        key[i] = grid_key(e[u], i);
+        if (g.score_out) g.score_out[(size_t)p * g.n + i] = e[u];
+      }
+    }
   }
   __syncthreads();
   // local maxima over the neighbour pairs (coalesced 4-byte loads, each pair once): of every pair the
@@ -2092,10 +2106,20 @@ __global__ void __launch_bounds__(kCandThreads, 4) k_grid_candidates(const Align
   unsigned char* notmax = reinterpret_cast<unsigned char*>(key + nkeys);
   for (int i = threadIdx.x; i < g.n; i += blockDim.x) notmax[i] = 0;
   __syncthreads();
-  for (int e = threadIdx.x; e < g.npairs; e += blockDim.x) {
-    const unsigned w = __ldg(g.pairs + e);
-    const int i = (int)(w >> 14), j = (int)(w & 0x3FFFu);
-    notmax[key[i] > key[j] ? j : i] = 1;
+  for (int e0 = threadIdx.x; e0 < g.npairs; e0 += kBatch * blockDim.x) {
+    unsigned w[kBatch];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      const int e = e0 + u * blockDim.x;
+      w[u] = e < g.npairs ? __ldg(g.pairs + e) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (w[u] != 0xFFFFFFFFu) {
+        const int i = (int)(w[u] >> 14), j = (int)(w[u] & 0x3FFFu);
+        notmax[key[i] > key[j] ? j : i] = 1;
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < g.n; i += blockDim.x)
