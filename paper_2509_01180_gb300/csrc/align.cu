@@ -363,83 +363,6 @@ __device__ __forceinline__ Eval eval_one(const float4* __restrict__ tab, int Lb,
   return e[0];
 }
 
-// Score only (no gradient) of C rotations at band L, one lane per rotation: the d recursion without its
-// beta derivative, for grid evaluations.
-template <int C>
-__device__ void eval_scores(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C],
-                            const float* __restrict__ lbin, float (&out)[C]) {
-  float xb[C], lcc[C], lss[C];
-  float2 R1[C], R2[C], Ed2[C], Wrow[C];
-#pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
-    const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
-    const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
-    const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
-    xb[j] = (cb - sb) * (cb + sb);
-    lcc[j] = log2f(fmaxf(cb, 1e-30f));
-    lss[j] = log2f(fmaxf(sb, 1e-30f));
-    const float2 Es = cconj(es);
-    R1[j] = cmul(Es, ed);
-    R2[j] = cmul(Es, cconj(ed));
-    const float2 Ed = cconj(ed);
-    Ed2[j] = cmul(Ed, Ed);
-    Wrow[j] = make_float2(1.f, 0.f);
-    out[j] = 0.f;
-  }
-  for (int m = 0; m <= L; ++m) {
-    const int w = 2 * m + 1;
-    const float4* rowp = tab + tab_base(m, Lb);
-    const float fm2 = (float)(m * m);
-    float2 P1[C], P2[C];
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      // n = -m: phases Es^0 ed^{-m}... as in eval_rotations with qg = 0: P1 = Wrow, P2 = conj(Wrow)
-      P1[j] = Wrow[j];
-      P2[j] = cconj(Wrow[j]);
-    }
-    for (int n = -m; n <= m; ++n) {
-      const float lb = __ldg(lbin + m * kBinStride + m + n);
-      const float fa = (float)(m + n), fd = (float)(m - n);
-      const bool odd = (m - n) & 1;
-      const float4* ep = rowp + (n + m);
-      const float4 xv = *ep;
-      float e1[C], e2[C], a1r[C], a1i[C], a2r[C], a2i[C];
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        float d = exp2f(lb + fa * lcc[j] + fd * lss[j]);
-        d = odd ? -d : d;
-        a1r[j] = d * xv.x; a1i[j] = d * xv.y; a2r[j] = d * xv.z; a2i[j] = d * xv.w;
-        e1[j] = d;
-        e2[j] = 0.f;
-      }
-      const float mn = (float)(m * n), fn2 = (float)(n * n);
-      for (int l = m + 1; l <= L; ++l) {
-        const float4 k0 = c_ecoef[l];
-        ep += w;
-        const float4 X = *ep;
-        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const float en = fmaf(fmaf(-mn, k0.x, xb[j]), e1[j], -g0 * e2[j]);
-          a1r[j] = fmaf(en, X.x, a1r[j]); a1i[j] = fmaf(en, X.y, a1i[j]);
-          a2r[j] = fmaf(en, X.z, a2r[j]); a2i[j] = fmaf(en, X.w, a2i[j]);
-          e2[j] = e1[j];
-          e1[j] = en;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        out[j] += (P1[j].x * a1r[j] - P1[j].y * a1i[j]) + (P2[j].x * a2r[j] - P2[j].y * a2i[j]);
-        P1[j] = cmul(P1[j], R1[j]);
-        P2[j] = cmul(P2[j], R2[j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < C; ++j) Wrow[j] = cmul(Wrow[j], Ed2[j]);
-  }
-}
-
 struct EvalH {
   float S, gx, gy, gz;
   float hxx, hxy, hxz, hyy, hyz, hzz;  // symmetric body-frame Hessian
@@ -1986,8 +1909,6 @@ __device__ __forceinline__ unsigned long long grid_key(float s, int i) {
 struct GridArgs {
   const float4* q;
   int n, npow2;
-  const int* off;
-  const int* nbr;
   int L;
   float4* starts_out;   // [B][S]
   int* index_out;       // [B][S] or NULL
@@ -2015,9 +1936,11 @@ __global__ void __launch_bounds__(128) k_cand_tables(const AlignArgs a, int L, i
 }
 
 // Wigner coefficients of the grid rotations at band L: for rotation i and orbit-table entry (m, l, n) the
-// factor e_l (Re P1, -Im P1, Re P2, -Im P2) that eval_scores multiplies that entry by, so that the band-L
-// score of a subtomogram is the dot product of its orbit table with row i -- a dense contraction over
-// all subtomograms and grid rotations.  One thread per rotation, the recursion and phases of eval_scores.
+// factor e_l (Re P1, -Im P1, Re P2, -Im P2) -- the rescaled d-recursion value of the orbit at degree l
+// times the orbit's two phases, as in eval_rotations without the beta derivative -- so that the band-L
+// score of a subtomogram, Re sum over entries of P1 e_l (x + iy) + P2 e_l (z + iw), is the dot product of
+// its orbit table with row i: a dense contraction over all subtomograms and grid rotations.  One thread
+// per rotation; the phases advance along the row (n += 1) by the ratios R1, R2.
 __global__ void __launch_bounds__(128) k_grid_coef(const float4* __restrict__ gq, int n, int n_pad, int L, int Kf4,
                                                    const float* __restrict__ lbin, float4* __restrict__ coef) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -2352,7 +2275,7 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
   if (el != cudaSuccess) st = fail(BH_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(el));
   if (st == BH_OK) st = sgemm_nt(reinterpret_cast<const float*>(X), reinterpret_cast<const float*>(coef), scores, B_pad, n_pad, 4 * Kf4, cs);
   if (st == BH_OK) {
-    GridArgs g{grid->d_q, grid->n, grid->npow2, grid->d_off, grid->d_nbr, L,
+    GridArgs g{grid->d_q, grid->n, grid->npow2, L,
                reinterpret_cast<float4*>(starts_out), index_out, grid_score_out, scores, n_pad,
                grid->d_pairs, grid->n_pairs};
     static std::atomic<int> have{0};
