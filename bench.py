@@ -585,7 +585,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="serving leg duration, the 60 s window of the serving workload (0 = skip)")
-    ap.add_argument("--serve-newton-seconds", type=float, default=20.0, help="duration of the Newton serving leg")
+    ap.add_argument("--serve-newton-seconds", type=float, default=60.0, help="duration of the Newton serving leg")
     ap.add_argument("--mixed-scale", type=float, default=1.0, help="class-count multiplier of the mixed workload")
     ap.add_argument("--no-autotune", action="store_true", help="use --group/--starts-per-thread instead of tuning")
     ap.add_argument("--group", type=int, default=4, help="lanes per start (group) with --no-autotune")
