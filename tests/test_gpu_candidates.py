@@ -116,6 +116,37 @@ def test_candidates_match_oracle(dev, n, S):
     p.destroy()
 
 
+def test_grid_factors_cached_per_band(dev):
+    """The grid's Wigner factors are built on the first call for a band and reused: repeated calls, calls
+    for another band in between, and a second plan sharing the grid give bitwise the same scores and
+    candidates; each band's scores match the oracle."""
+    w, Bs, p, c, t, F = _pair16_case(dev, 3, 4)
+    g = synth.super_fibonacci(500)
+    grid = bh.bh_grid_create(g, math.radians(40.0))
+    tm, sub = c[0].contiguous(), c[1:].contiguous()
+    first = [x.cpu().numpy() for x in bh.bh_candidates(p, grid, tm, sub, 4, 6, with_index=True, with_scores=True)]
+    other = [x.cpu().numpy() for x in bh.bh_candidates(p, grid, tm, sub, 2, 6, with_index=True, with_scores=True)]
+    again = [x.cpu().numpy() for x in bh.bh_candidates(p, grid, tm, sub, 4, 6, with_index=True, with_scores=True)]
+    p2 = bh.bh_plan_create(16, 8, 8 * math.pi, bh.BH_MODE_FP32)
+    c2 = bh.bh_expand(p2, torch.from_numpy(np.concatenate([w.template[None], w.vols])).to(dev))
+    assert torch.equal(c2, c)  # the same coefficients from a second plan
+    third = [x.cpu().numpy() for x in bh.bh_candidates(p2, grid, c2[0].contiguous(), c2[1:].contiguous(), 4, 6,
+                                                         with_index=True, with_scores=True)]
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)
+    for a, b in zip(first, third):
+        assert np.array_equal(a, b)
+    for L, res in ((4, first), (2, other)):
+        for b in range(w.B):
+            ref = candidates.grid_scores(align.build_xi(Bs, t, F[b], L), g, L)
+            scale = math.sqrt(sum(np.sum(np.abs(ball.split_by_degree(Bs, t)[l]) ** 2) for l in range(L + 1)) *
+                              sum(np.sum(np.abs(ball.split_by_degree(Bs, F[b])[l]) ** 2) for l in range(L + 1)))
+            assert np.abs(res[2][b].astype(np.float64) - ref).max() <= 1e-4 * scale, (L, b)
+    grid.destroy()
+    p2.destroy()
+    p.destroy()
+
+
 def test_candidate_pipeline_reaches_oracle_optimum(dev):
     """Sec. III pipeline: band-4 candidates -> marching ascent 4-8 from them; GPU vs oracle end to end."""
     L1, S, n, radius = 4, 8, 1000, math.radians(50.0)
