@@ -16,16 +16,20 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbh.so")
 
 BH_OK, BH_PENDING = 0, 1
-BH_ERR_ARG, BH_ERR_CUDA, BH_ERR_OOM, BH_ERR_BUDGET, BH_ERR_TIMEOUT, BH_ERR_BUSY, BH_ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+(BH_ERR_ARG, BH_ERR_CUDA, BH_ERR_OOM, BH_ERR_BUDGET, BH_ERR_TIMEOUT, BH_ERR_BUSY,
+ BH_ERR_UNSUPPORTED) = -1, -2, -3, -4, -5, -6, -7
 BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
 
 # every symbol include/bh.h declares (checked by the CPU tests)
-EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots", "bh_plan_create",
-           "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_plan_status", "bh_plan_probe_wait", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
-           "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts", "bh_grid_create", "bh_grid_destroy", "bh_grid_info",
-           "bh_grid_neighbors", "bh_candidates", "bh_wedge_create", "bh_wedge_destroy", "bh_wedge_coeffs",
-           "bh_wedge_norm", "bh_energy", "bh_autotune", "bh_autotune_newton", "bh_random_starts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit",
-           "bh_serve_poll", "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
+EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots",
+           "bh_plan_create", "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_plan_status",
+           "bh_plan_probe_wait", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
+           "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts",
+           "bh_grid_create", "bh_grid_destroy", "bh_grid_info", "bh_grid_neighbors", "bh_candidates",
+           "bh_wedge_create", "bh_wedge_destroy", "bh_wedge_coeffs", "bh_wedge_norm", "bh_energy",
+           "bh_autotune", "bh_autotune_newton", "bh_random_starts",
+           "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll", "bh_serve_wait",
+           "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
 
 
 class BHError(RuntimeError):
@@ -448,8 +452,9 @@ class Request(ctypes.Structure):
 
 class ServeCounters(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
-                ("express_batches", ctypes.c_uint64), ("in_place_batches", ctypes.c_uint64), ("queued", ctypes.c_uint64),
-                ("inflight_batches", ctypes.c_uint64), ("inflight_bytes", ctypes.c_size_t), ("staging_allocs", ctypes.c_uint64),
+                ("express_batches", ctypes.c_uint64), ("in_place_batches", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("inflight_batches", ctypes.c_uint64),
+                ("inflight_bytes", ctypes.c_size_t), ("staging_allocs", ctypes.c_uint64),
                 ("launch_ms_total", ctypes.c_double), ("launch_ms_max", ctypes.c_double)]
 
 
@@ -473,8 +478,9 @@ def _serve_sigs(L):
     L.bh_serve_pause.argtypes = [vp, i]
     L.bh_serve_stats.argtypes = [vp, ctypes.POINTER(ServeCounters)]
     L.bh_serve_destroy.argtypes = [vp]
-    for n in ("bh_random_starts", "bh_autotune", "bh_energy", "bh_align_shifts", "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll",
-              "bh_serve_wait", "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"):
+    for n in ("bh_random_starts", "bh_autotune", "bh_energy", "bh_align_shifts", "bh_serve_create",
+              "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll", "bh_serve_wait", "bh_serve_pause",
+              "bh_serve_stats", "bh_serve_destroy"):
         getattr(L, n).restype = i
     L._serve_ready = True
 
