@@ -95,3 +95,62 @@ def test_hessian_pin_catches_mistakes(monkeypatch, mutant):
     rng = np.random.default_rng(2)
     small = (Bs, rng.normal(size=Bs.Nb) + 1j * rng.normal(size=Bs.Nb), rng.normal(size=Bs.Nb) + 1j * rng.normal(size=Bs.Nb))
     assert _fails(ta.test_hessian_matches_mixed_differences, small)
+
+
+# ---------------------------------------------------------------------------- step control (Sec. II-C, Sec. III)
+def _mutant(module, name, old, new):
+    """`module.name` recompiled from its source with one text change (the planted mistake)."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(module, name)))
+    assert src.count(old) == 1, old
+    ns = dict(vars(module))
+    exec(compile(src.replace(old, new), f"<mutant of {name}>", "exec"), ns)
+    return ns[name]
+
+
+def _step_pins_fail(kind):
+    from tests import test_oracle_steps as ts
+    if kind == "ascend":
+        runs = [(ts.test_ascent_steps_band1, k) for k in range(1, 6)] + [(ts.test_ascent_two_bands,)]
+    else:
+        runs = [(ts.test_newton_steps_band1, k) for k in range(1, 4)] + [
+            (ts.test_newton_damping_restarts_per_band,), (ts.test_newton_gradient_step_then_newton_step,)]
+    return any(_fails(*r) for r in runs)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("h = min(1.5 * h, hmax)", "h = min(2.0 * h, hmax)"),                       # growth x2 instead of x1.5
+    ("h = h / 2", "h = h / 4"),                                                 # shrink x1/4 instead of x1/2
+    ("        h = h0\n", "        h = h if L != stages[0] else h0\n"),          # no restart of h per band
+    ("math.pi / (2 * L), math.pi / L", "math.pi / (2 * L), math.pi / (2 * L)"),  # hmax = pi/(2L)
+    ("math.pi / (2 * L), math.pi / L", "math.pi / L, math.pi / L"),              # h0 = pi/L
+])
+def test_step_pins_catch_ascent_mistakes(monkeypatch, old, new):
+    monkeypatch.setattr(align, "ascend", _mutant(align, "ascend", old, new))
+    assert _step_pins_fail("ascend")
+
+
+@pytest.mark.parametrize("old,new", [
+    ("lam = min(1.0, 2 * lam)", "lam = 2 * lam"),                              # damping not capped at 1
+    ("lam = lam / 2", "lam = lam / 4"),                                        # shrink x1/4 instead of x1/2
+    ("        lam = 1.0\n", "        lam = lam if L != stages[0] else 1.0\n"),  # no restart of lam per band
+    ("math.pi / (2 * L), math.pi / L", "math.pi / (2 * L), math.pi / (2 * L)"),  # clip at pi/(2L)
+    ("if np.linalg.eigvalsh(H).max() < 0:", "if True:"),                        # Newton step without the test
+])
+def test_step_pins_catch_newton_mistakes(monkeypatch, old, new):
+    monkeypatch.setattr(align, "newton", _mutant(align, "newton", old, new))
+    assert _step_pins_fail("newton")
+
+
+# ---------------------------------------------------------------------------- DFT power of the template (Sec. II-B)
+@pytest.mark.parametrize("old,new", [
+    ("tb[flat] = np.asarray(tvol, np.float64).ravel()[flat]", "tb[:] = np.asarray(tvol, np.float64).ravel()"),  # no ball
+    ("sel = (r > 0) & (r < N / 2)", "sel = (r > 0) & (r <= N / 2)"),            # |k| = N/2 kept
+    ('kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")', 'kx, ky, kz = np.meshgrid(k, k, k, indexing="ij")'),  # axes
+])
+def test_dft_power_pin_catches_mistakes(monkeypatch, old, new):
+    from oracle import wedge
+    from tests import test_oracle_wedge as twd
+    monkeypatch.setattr(wedge, "dft_power", _mutant(wedge, "dft_power", old, new))
+    assert _fails(twd.test_dft_power_is_the_direct_dft_of_the_ball_restricted_volume)

@@ -123,3 +123,42 @@ def test_wedge_pins_catch_mistakes(monkeypatch, mutant, pair):
         bad = wedge.Wedge(wd.L, [np.conj(x) for x in wd.q], wd.w, wd.c0)
         with pytest.raises(AssertionError):
             test_denominator_equals_the_sum_over_dft_samples((w, bad))
+
+
+def direct_dft_power(vol: np.ndarray):
+    """|T(k)|^2 by the definition T(k) = sum_{voxels v in the ball} t(v) exp(-2 pi i k.v / N), for every integer
+    frequency vector k = (kx, ky, kz) in [-N/2, N/2)^3 with 0 < |k| < N/2 (kx along the array's last axis),
+    returned as rows (k/|k|, |T(k)|^2), and |T(0)|^2.  O(N^6), for tiny N only."""
+    N = vol.shape[0]
+    h = N // 2
+    rows = []
+    idx = np.arange(N)
+    z, y, x = np.meshgrid(idx, idx, idx, indexing="ij")
+    ball = (x - h) ** 2 + (y - h) ** 2 + (z - h) ** 2 < h * h
+    tv, xs, ys, zs = vol[ball], x[ball], y[ball], z[ball]
+    for kz in range(-h, h):
+        for ky in range(-h, h):
+            for kx in range(-h, h):
+                r2 = kx * kx + ky * ky + kz * kz
+                if r2 == 0 or r2 >= h * h:
+                    continue
+                T = np.sum(tv * np.exp(-2j * np.pi * (kx * xs + ky * ys + kz * zs) / N))
+                r = math.sqrt(r2)
+                rows.append((kx / r, ky / r, kz / r, abs(T) ** 2))
+    return np.array(rows), abs(np.sum(tv)) ** 2
+
+
+def test_dft_power_is_the_direct_dft_of_the_ball_restricted_volume():
+    """dft_power against the DFT written out on an 8^3 volume with no symmetry (random values): the same
+    multiset of (direction, power) pairs, the same count of frequencies, and the same |T(0)|^2."""
+    rng = np.random.default_rng(64)
+    vol = rng.normal(size=(8, 8, 8)) + np.linspace(0, 1, 8)[None, None, :]  # a ramp along x breaks symmetry
+    dirs, pw, c0 = wedge.dft_power(vol)
+    ref, c0_ref = direct_dft_power(vol)
+    assert len(pw) == len(ref)
+    got = np.concatenate([dirs, pw[:, None]], axis=1)
+    key = lambda a: np.lexsort((a[:, 3], np.round(a[:, 2], 9), np.round(a[:, 1], 9), np.round(a[:, 0], 9)))
+    got, ref = got[key(got)], ref[key(ref)]
+    assert np.allclose(got[:, :3], ref[:, :3], atol=1e-12)
+    assert np.allclose(got[:, 3], ref[:, 3], rtol=1e-10, atol=1e-10 * ref[:, 3].max())
+    assert abs(c0 - c0_ref) < 1e-10 * c0_ref
