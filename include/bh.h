@@ -62,6 +62,11 @@ extern "C" {
 #define BH_ERR_BUSY (-6)      /* serving: queue full, try again */
 #define BH_ERR_UNSUPPORTED (-7) /* the device or configuration is not supported (not sm_103) */
 
+/* marching schedules: at most BH_MAX_STAGES bands; a per-subtomogram schedule row (bh_align_opts.stage_table,
+   bh_choose_bands) is a band count followed by the bands */
+#define BH_MAX_STAGES 8
+#define BH_STAGE_ROW (BH_MAX_STAGES + 1)
+
 /* expansion arithmetic (bh_plan_opts.mode) */
 #define BH_MODE_FP32 0        /* plain FP32 FFMA GEMM */
 #define BH_MODE_BF16_SPLIT 1  /* tcgen05 BF16 tensor-core GEMM, hi/lo split: Xh*Th + Xh*Tl + Xl*Th, FP32 accum */
@@ -89,19 +94,27 @@ int bh_basis_roots(int Lmax, double lambda_max, int* K, double* lambda, double* 
 /* ------------------------------------------------------------------ plans */
 typedef struct bh_plan bh_plan;
 
+/* plan flags (bh_plan_opts.flags) */
+#define BH_PLAN_MATCH_ONLY 1  /* no expansion table or scratch: the matching calls only (score, alignment,
+                                 candidates, energy, re-scoring) on coefficients computed elsewhere */
+
 typedef struct {
   int N;             /* box edge in voxels: even, 4..256 */
   int Lmax;          /* largest degree: 0..64 */
   double lambda_max; /* radial cutoff; <= 0 selects pi * N / 2 */
   int mode;          /* BH_MODE_FP32 or BH_MODE_BF16_SPLIT */
   int max_batch;     /* volumes per internal expansion pass (sizes the scratch); <= 0 selects 512 */
+  int flags;         /* 0 or BH_PLAN_MATCH_ONLY */
 } bh_plan_opts;
 
 /*
  * Build a plan on the current CUDA device: roots and constants in FP64 on the host, the basis
  * table Psi[j][v] (real form, one row per coefficient slot, h^3 folded in) evaluated in FP64
- * and stored on the device in the arithmetic of `mode`, plus the expansion scratch.
- * The plan owns all of its device memory.  Creation is synchronous.
+ * and stored on the device in the arithmetic of `mode`, plus the expansion scratch.  With
+ * flags = BH_PLAN_MATCH_ONLY the table and scratch are left out (64^3, l <= 32: 13 GB fewer in
+ * BF16-split mode); the expansion calls and the shift search then fail with BH_ERR_ARG.
+ * The plan owns all of its device memory and must be used with its device current (other
+ * devices: BH_ERR_ARG).  Creation is synchronous.
  * Errors: BH_ERR_ARG (options), BH_ERR_OOM, BH_ERR_CUDA, BH_ERR_UNSUPPORTED (device is not
  * compute capability 10.3).
  */
@@ -186,6 +199,24 @@ int bh_energy(const bh_plan* plan, const float* tmpl, const float* sub, int B, i
               int n_templates, float* energy, void* stream);
 
 /*
+ * Marching bands chosen by the energy ratio (Fig. 1; Sec. II-C uses it to find high-energy bands and
+ * Sec. III picks its L_set = {7, 12, 33} with it; the rule below is this library's reading), per
+ * subtomogram: E_l = sum_{m,m'} |xi^l_{mm'}|^2 for l = 0..L (xi summed in FP32 over k, the energies in
+ * FP64), Ratio(L') = sum_{l>L'} E_l / sum_{l<=L} E_l; band j is the smallest L' >= L_min with
+ * Ratio(L') <= thresholds[j]; a band equal to the previous one is written once.  The rows feed
+ * bh_align_batch (opts.stage_table) and bh_refine_fp64 without a round trip to the host.
+ *   L             1..Lmax: the highest degree counted (and so the highest band a row can hold)
+ *   tmpl_index, n_templates   as bh_align_opts (tmpl_index may be NULL)
+ *   thresholds    host, n_thresholds doubles in (0, 1), strictly decreasing; n_thresholds 1..BH_MAX_STAGES
+ *   L_min         1..L: the lowest band
+ *   stage_table   device, B * BH_STAGE_ROW ints: row b = (number of bands, bands ascending)
+ *   energy        device, B * (L+1) floats or NULL: E_l
+ */
+int bh_choose_bands(const bh_plan* plan, const float* tmpl, const float* sub, int B, int L, const int* tmpl_index,
+                    int n_templates, const double* thresholds, int n_thresholds, int L_min, int* stage_table,
+                    float* energy, void* stream);
+
+/*
  * Score, gradient and Hessian of Eq. 2 (Newton steps, Sec. III) at S rotations per subtomogram, band L.
  * The Hessian is the second derivative of S(R exp(eps.J)) at eps = 0 (body frame, symmetric),
  * H_ij = -Re sum_l sum_{m,m'} xi^l_{mm'} [D^l(R) (J_i J_j + J_j J_i)/2]_{mm'}; it is evaluated through
@@ -218,10 +249,20 @@ typedef struct {
                              group (starts_per_thread 0 or 1); `group` may also be 32; 0 picks a
                              default (up to a warp per start when S is small and the band large) */
   const struct bh_wedge* wedge; /* NULL, or the missing-wedge norm from bh_wedge_create: maximise the
-                             constrained score C(R) = S(R) / sqrt(Dn(R)) (Sec. II-B) with the
-                             ascent's step rule and marching instead of S(R); one template (no
-                             tmpl_index), newton 0, starts_per_thread 0 or 1; score_out then holds C */
+                             constrained score C(R) = S(R) / sqrt(Dn(R)), the common-region form of
+                             Sec. II-B, with the ascent's step rule and marching instead of S(R); one
+                             template (no tmpl_index), newton 0, starts_per_thread 0 or 1; score_out then
+                             holds C.  Diagnostic, off by default: on voxel data with a missing wedge it
+                             reproduces its FP64 reading but lands farther from the ground truth than the
+                             plain score (1.8 against 1.0 degrees median on the 32^3 batch) */
+  const int* stage_table;  /* device, B * BH_STAGE_ROW ints or NULL: a marching schedule per subtomogram,
+                             row b = (count, band_1 < band_2 < ...), e.g. from bh_choose_bands.  `stages`
+                             then gives the largest band any row may use (shared memory, kernel variant)
+                             and the schedule of rows whose count is 0; bands are clamped to
+                             1..stages[nstages-1] and a band not above its predecessor is skipped.  With
+                             refine_fp64 each subtomogram is re-scored at its own last band */
 } bh_align_opts;
+
 
 /*
  * Multi-start gradient ascent with frequency marching (Sec. II-C) for B subtomograms, in one
@@ -243,6 +284,24 @@ typedef struct {
 int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int B,
                    const float* starts, int S, const int* stages, int nstages, int steps,
                    float* quat_out, float* score_out, const bh_align_opts* opts, void* stream);
+
+/*
+ * The precision form's final refinement as a call of its own (bh_align_batch runs the same step when
+ * opts->refine_fp64 = K): for every subtomogram, the K starts with the largest FP32 scores in
+ * start_score (ties: lowest index) are scored at band L with the d-recursion, seeds, phases and sums in
+ * FP64 (Eq. 2; the orbit table of P_l xi^l is rounded to FP32 once per entry), and the best of them on
+ * the FP64 score is written to quat_out / score_out (rounded to float) / score64_out.
+ *   start_quat   device, B * S * 4 floats: final rotation of every start (opts->start_quat_out)
+ *   start_score  device, B * S floats: their FP32 scores (opts->start_score_out)
+ *   L            band, 0..Lmax;  K  1..min(64, S)
+ *   tmpl_index   device, B ints or NULL (n_templates rows in tmpl), as in bh_align_opts
+ *   stage_table  device, B * BH_STAGE_ROW ints or NULL (see bh_align_opts.stage_table): each subtomogram
+ *                is then re-scored at the last band of its row (bands clamped to 1..L; L >= 1)
+ *   score64_out  device, B doubles or NULL
+ */
+int bh_refine_fp64(const bh_plan* plan, const float* tmpl, const float* sub, int B, const float* start_quat,
+                   const float* start_score, int S, int L, int K, const int* tmpl_index, int n_templates,
+                   const int* stage_table, float* quat_out, float* score_out, double* score64_out, void* stream);
 
 /* ------------------------------------------------------------------ shift search */
 /*

@@ -25,6 +25,10 @@ Readings where the paper is silent, garbled or ambiguous:
   * Selection: argmax over starts of the final-stage score; ties within 1e-12 |S|
     go to the lowest start index.
   * Energy ratio: the Fig. 1 caption omits the sums over m, m'; the reading sums them.
+  * Band selection (Sec. II-C: the energy ratio picks high-energy bands; Sec. III: L_set chosen with it;
+    no rule is printed): for thresholds tau_1 > tau_2 > ... > tau_n in (0, 1) and a lowest band L_min >= 1,
+    band j is the smallest L >= L_min whose remaining energy Ratio(L) is at most tau_j (Ratio(Lmax) = 0,
+    so it exists); equal consecutive bands are kept once, so the marching schedule is strictly increasing.
   * Newton steps (Sec. III names them, without details): the Hessian is the second derivative of
     S(R exp(eps.J)) at eps = 0, H_ij = -Re sum xi^l_{mm'} [D^l(R) (J_i J_j + J_j J_i) / 2]_{mm'}.
     Per stage with band L, T iterations: stop if |g| <= 1e-12 |S|; if H is negative definite the
@@ -205,6 +209,21 @@ def energy_ratio(xi: list[np.ndarray]) -> np.ndarray:
     tot = e.sum()
     tail = np.concatenate([np.cumsum(e[::-1])[::-1][1:], [0.0]])
     return tail / tot if tot > 0 else np.zeros_like(e)
+
+
+def choose_bands(xi: list[np.ndarray], thresholds, L_min: int = 1) -> list[int]:
+    """Marching bands picked by the energy ratio of Fig. 1 (reading above): for each threshold tau_j, in the
+    given (decreasing) order, the smallest L >= L_min with Ratio(L) <= tau_j; repeats dropped."""
+    r = energy_ratio(xi)
+    Lmax = len(r) - 1
+    if not 1 <= L_min <= Lmax:
+        raise ValueError("L_min must lie in 1..Lmax")
+    bands = []
+    for tau in thresholds:
+        L = next(L for L in range(L_min, Lmax + 1) if r[L] <= tau)
+        if not bands or L > bands[-1]:
+            bands.append(L)
+    return bands
 
 
 def rotate_coeffs(basis: Basis, coeffs: np.ndarray, q) -> np.ndarray:

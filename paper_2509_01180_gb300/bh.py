@@ -19,14 +19,17 @@ BH_OK, BH_PENDING = 0, 1
 (BH_ERR_ARG, BH_ERR_CUDA, BH_ERR_OOM, BH_ERR_BUDGET, BH_ERR_TIMEOUT, BH_ERR_BUSY,
  BH_ERR_UNSUPPORTED) = -1, -2, -3, -4, -5, -6, -7
 BH_MODE_FP32, BH_MODE_BF16_SPLIT = 0, 1
+BH_PLAN_MATCH_ONLY = 1
+BH_MAX_STAGES = 8
+BH_STAGE_ROW = BH_MAX_STAGES + 1
 
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots",
            "bh_plan_create", "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_plan_status",
            "bh_plan_probe_wait", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
-           "bh_align_batch", "bh_align_shifts_workspace", "bh_align_shifts",
+           "bh_align_batch", "bh_refine_fp64", "bh_align_shifts_workspace", "bh_align_shifts",
            "bh_grid_create", "bh_grid_destroy", "bh_grid_info", "bh_grid_neighbors", "bh_candidates",
-           "bh_wedge_create", "bh_wedge_destroy", "bh_wedge_coeffs", "bh_wedge_norm", "bh_energy",
+           "bh_wedge_create", "bh_wedge_destroy", "bh_wedge_coeffs", "bh_wedge_norm", "bh_energy", "bh_choose_bands",
            "bh_autotune", "bh_autotune_newton", "bh_random_starts",
            "bh_serve_create", "bh_serve_add_template", "bh_serve_submit", "bh_serve_poll", "bh_serve_wait",
            "bh_serve_pause", "bh_serve_stats", "bh_serve_destroy"]
@@ -40,14 +43,14 @@ class BHError(RuntimeError):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("Lmax", ctypes.c_int), ("lambda_max", ctypes.c_double),
-                ("mode", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("mode", ctypes.c_int), ("max_batch", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class AlignOpts(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int), ("tmpl_index", ctypes.c_void_p), ("n_templates", ctypes.c_int),
                 ("start_quat_out", ctypes.c_void_p), ("start_score_out", ctypes.c_void_p),
                 ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int), ("newton", ctypes.c_int),
-                ("wedge", ctypes.c_void_p)]
+                ("wedge", ctypes.c_void_p), ("stage_table", ctypes.c_void_p)]
 
 
 _lib = None
@@ -77,6 +80,8 @@ def lib() -> ctypes.CDLL:
         L.bh_score_grad.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp]
         L.bh_score_hess.argtypes = [vp, vp, vp, i, vp, i, i, vp, vp, vp, vp]
         L.bh_align_batch.argtypes = [vp, vp, vp, i, vp, i, vp, i, i, vp, vp, ctypes.POINTER(AlignOpts), vp]
+        L.bh_refine_fp64.argtypes = [vp, vp, vp, i, vp, vp, i, i, i, vp, i, vp, vp, vp, vp, vp]
+        L.bh_choose_bands.argtypes = [vp, vp, vp, i, i, vp, i, vp, i, i, vp, vp, vp]
         L.bh_grid_create.argtypes = [ctypes.POINTER(vp), vp, i, d]
         L.bh_grid_destroy.argtypes = [vp]
         L.bh_grid_info.argtypes = [vp, vp, vp, vp]
@@ -142,6 +147,7 @@ class Plan:
         o = PlanOpts()
         _check(lib().bh_plan_info(handle, ctypes.byref(o)), "bh_plan_info")
         self.N, self.Lmax, self.lambda_max, self.mode, self.max_batch = o.N, o.Lmax, o.lambda_max, o.mode, o.max_batch
+        self.flags = o.flags
         Nb, V = ctypes.c_int(), ctypes.c_int()
         offs = np.zeros(self.Lmax + 2, dtype=np.int32)
         _check(lib().bh_plan_layout(handle, ctypes.addressof(Nb), ctypes.addressof(V), offs.ctypes.data),
@@ -160,8 +166,9 @@ class Plan:
             pass
 
 
-def bh_plan_create(N: int, Lmax: int, lambda_max: float = 0.0, mode: int = BH_MODE_FP32, max_batch: int = 0) -> Plan:
-    o = PlanOpts(N, Lmax, float(lambda_max), mode, max_batch)
+def bh_plan_create(N: int, Lmax: int, lambda_max: float = 0.0, mode: int = BH_MODE_FP32, max_batch: int = 0,
+                   flags: int = 0) -> Plan:
+    o = PlanOpts(N, Lmax, float(lambda_max), mode, max_batch, flags)
     h = ctypes.c_void_p()
     _check(lib().bh_plan_create(ctypes.byref(h), ctypes.byref(o)), "bh_plan_create")
     return Plan(h.value)
@@ -231,7 +238,8 @@ def bh_score_hess(plan: Plan, tmpl, sub, quats, L: int, stream=None):
 # ------------------------------------------------------------------ alignment
 def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
                    n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None,
-                   refine_fp64: int = 0, starts_per_thread: int = 0, newton: bool = False, wedge=None):
+                   refine_fp64: int = 0, starts_per_thread: int = 0, newton: bool = False, wedge=None,
+                   stage_table=None):
     """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
     import torch
     B, S = starts.shape[0], starts.shape[1]
@@ -248,6 +256,9 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     o.refine_fp64 = refine_fp64
     o.newton = int(bool(newton))
     o.wedge = wedge.handle if wedge is not None else None
+    if stage_table is not None:
+        _need(stage_table, "torch.int32", B * BH_STAGE_ROW, "stage_table")
+        o.stage_table = _ptr(stage_table)
     sq = ss = None
     if per_start or refine_fp64:
         sq = torch.empty((B, S, 4), dtype=torch.float32, device=dev)
@@ -261,6 +272,29 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     if per_start:
         return quat, score, sq, ss
     return quat, score
+
+
+def bh_refine_fp64(plan: Plan, tmpl, sub, start_quat, start_score, L: int, K: int, tmpl_index=None,
+                   n_templates: int = 0, quat_out=None, score_out=None, score64_out=None, stream=None,
+                   stage_table=None):
+    """FP64 re-score of the K best starts at band L: returns (quat (B,4), score (B,), score64 (B,) float64)."""
+    import torch
+    B, S = start_quat.shape[0], start_quat.shape[1]
+    dev = sub.device
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    _need(start_quat, "torch.float32", B * S * 4, "start_quat")
+    _need(start_score, "torch.float32", B * S, "start_score")
+    quat = quat_out if quat_out is not None else torch.empty((B, 4), dtype=torch.float32, device=dev)
+    score = score_out if score_out is not None else torch.empty((B,), dtype=torch.float32, device=dev)
+    s64 = score64_out if score64_out is not None else torch.empty((B,), dtype=torch.float64, device=dev)
+    if tmpl_index is not None:
+        _need(tmpl_index, "torch.int32", B, "tmpl_index")
+    if stage_table is not None:
+        _need(stage_table, "torch.int32", B * BH_STAGE_ROW, "stage_table")
+    _check(lib().bh_refine_fp64(plan.handle, _ptr(tmpl), _ptr(sub), B, _ptr(start_quat), _ptr(start_score), S, L, K,
+                                _ptr(tmpl_index), n_templates, _ptr(stage_table), _ptr(quat), _ptr(score), _ptr(s64),
+                                _stream(stream)), "bh_refine_fp64")
+    return quat, score, s64
 
 
 # ------------------------------------------------------------------ random starts
@@ -413,6 +447,32 @@ def bh_energy(plan: Plan, tmpl, sub, L: int, tmpl_index=None, n_templates: int =
     tail = ed.flip(1).cumsum(1).flip(1)
     ratio = torch.cat([tail[:, 1:], torch.zeros_like(tail[:, :1])], 1) / ed.sum(1, keepdim=True).clamp_min(1e-300)
     return e, ratio
+
+
+def bh_choose_bands(plan: Plan, tmpl, sub, L: int, thresholds, L_min: int = 1, tmpl_index=None,
+                    n_templates: int = 0, stage_table=None, with_energy: bool = False, stream=None):
+    """Per-subtomogram marching bands from the energy ratio: returns (stage_table (B, BH_STAGE_ROW) int32,
+    energy (B, L+1) or None)."""
+    import torch
+    B = sub.shape[0]
+    _need(sub, "torch.float32", B * plan.Nb * 2, "sub")
+    thr = np.ascontiguousarray(np.asarray(thresholds, dtype=np.float64))
+    tab = stage_table if stage_table is not None else torch.empty((B, BH_STAGE_ROW), dtype=torch.int32,
+                                                                   device=sub.device)
+    _need(tab, "torch.int32", B * BH_STAGE_ROW, "stage_table")
+    e = torch.empty((B, L + 1), dtype=torch.float32, device=sub.device) if with_energy else None
+    if tmpl_index is not None:
+        _need(tmpl_index, "torch.int32", B, "tmpl_index")
+    _check(lib().bh_choose_bands(plan.handle, _ptr(tmpl), _ptr(sub), B, L, _ptr(tmpl_index), n_templates,
+                                 thr.ctypes.data, len(thr), L_min, _ptr(tab), _ptr(e), _stream(stream)),
+           "bh_choose_bands")
+    return tab, e
+
+
+def stage_rows(table) -> list[list[int]]:
+    """Host view of a stage table: the bands of every row."""
+    t = table.cpu().numpy() if hasattr(table, "cpu") else np.asarray(table)
+    return [[int(x) for x in r[1:1 + int(r[0])]] for r in t]
 
 
 class TuneResult(ctypes.Structure):

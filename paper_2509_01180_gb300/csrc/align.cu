@@ -53,6 +53,7 @@ constexpr int kBinStride = 2 * kMaxL + 1;
 __constant__ float4 c_ecoef[kMaxL + 2];
 
 constexpr int kMaxStages = 8;
+static_assert(kMaxStages == BH_MAX_STAGES, "schedule rows of the C ABI");
 constexpr int kMaxThreads = 512;  // threads per CTA (S * G rounded up to a warp)
 
 struct AlignArgs {
@@ -67,7 +68,8 @@ struct AlignArgs {
   int nstages;
   int stages[kMaxStages];
   int steps;
-  int Lb;  // band of the shared-memory table
+  int Lb;  // band of the shared-memory table (the largest band any subtomogram of the launch uses)
+  const int* stage_table;  // [B][kMaxStages + 1] (count, bands) per subtomogram, or NULL: stages[] for all
   const float* P;       // [orbit table of band Lmax] P_l(m,n) = prod_{j=m+1..l} j(2j-1)/u_j
   const float* lbin;    // [m][m+n] 0.5 log2 C(2m, m+n), row stride 2 kMaxL + 1
   float4* quat_out;
@@ -534,6 +536,35 @@ __device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p)
   return a.tmpl + (size_t)t * a.lay.Nb;
 }
 
+// Marching schedule of subtomogram p into shared memory: sched[0] = number of bands, sched[1..] the bands.
+// From the per-subtomogram table when the launch has one -- each band clamped to 1..a.Lb and kept only if
+// it exceeds the previous one, so that a malformed row can neither index past the shared-memory table
+// (sized for a.Lb) nor stall the marching; an empty row falls back to the launch's own schedule -- else the
+// launch's schedule.  Ends with a barrier.
+__device__ void load_schedule(const AlignArgs& a, int p, int* sched) {
+  if (threadIdx.x == 0) {
+    int n = 0;
+    if (a.stage_table) {
+      const int* row = a.stage_table + (size_t)p * (kMaxStages + 1);
+      const int cnt = min(max(row[0], 0), kMaxStages);
+      int last = 0;
+      for (int i = 0; i < cnt; ++i) {
+        const int L = min(max(row[1 + i], 1), a.Lb);
+        if (L > last) {
+          sched[1 + n++] = L;
+          last = L;
+        }
+      }
+    }
+    if (n == 0) {
+      for (int i = 0; i < a.nstages; ++i) sched[1 + i] = a.stages[i];
+      n = a.nstages;
+    }
+    sched[0] = n;
+  }
+  __syncthreads();
+}
+
 // Minimum resident CTAs per SM requested from the compiler for a block of NT threads.  Small blocks (one
 // or two warps) keep 8 resident CTAs (shared memory holds 7 orbit tables of band 16); larger blocks are
 // used when the table is large and few CTAs fit, so they get at least 128 registers per thread.
@@ -544,10 +575,13 @@ template <int G, int NT>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align(const AlignArgs a) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
+  __shared__ int sched[kMaxStages + 1];
+  load_schedule(a, p, sched);
+  const int Lb = sched[sched[0]];
   const int s = threadIdx.x / G, qg = threadIdx.x % G;
   const bool active = s < a.S;
   const int se = active ? s : s % a.S;  // lanes past the last start shadow a real one and write nothing
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, Lb, threadIdx.x,
               blockDim.x);
   __syncthreads();
 
@@ -555,11 +589,11 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align(const AlignArgs a)
   Eval cur;
   cur.S = 0.f;
   cur.gx = cur.gy = cur.gz = 0.f;
-  for (int st = 0; st < a.nstages; ++st) {
-    const int L = a.stages[st];
+  for (int st = 0; st < sched[0]; ++st) {
+    const int L = sched[1 + st];
     const float hmax = 3.14159265358979f / (float)L;
     float h = 0.5f * hmax;
-    cur = eval_one<G>(smem_tab, a.Lb, L, q, qg, a.lbin);
+    cur = eval_one<G>(smem_tab, Lb, L, q, qg, a.lbin);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -568,7 +602,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align(const AlignArgs a)
       sincosf(stop ? 0.f : 0.5f * h, &sh, &ch);
       const float4 dq = make_float4(ch, sh * cur.gx * inv, sh * cur.gy * inv, sh * cur.gz * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const Eval tr = eval_one<G>(smem_tab, a.Lb, L, qt, qg, a.lbin);
+      const Eval tr = eval_one<G>(smem_tab, Lb, L, qt, qg, a.lbin);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -694,20 +728,23 @@ template <int G, int NT>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_newton(const AlignArgs a) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
+  __shared__ int sched[kMaxStages + 1];
+  load_schedule(a, p, sched);
+  const int Lb = sched[sched[0]];
   const int s = threadIdx.x / G, qg = threadIdx.x % G;
   const bool active = s < a.S;
   const int se = active ? s : s % a.S;
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, Lb, threadIdx.x,
               blockDim.x);
   __syncthreads();
   float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
   EvalH cur;
   cur.S = 0.f;
-  for (int st = 0; st < a.nstages; ++st) {
-    const int L = a.stages[st];
+  for (int st = 0; st < sched[0]; ++st) {
+    const int L = sched[1 + st];
     const float hmax = 3.14159265358979f / (float)L, h0 = 0.5f * hmax;
     float lam = 1.f;
-    cur = eval_hess<G>(smem_tab, a.Lb, L, q, qg, a.lbin);
+    cur = eval_hess<G>(smem_tab, Lb, L, q, qg, a.lbin);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -719,7 +756,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_newton(const AlignArgs a
       sincosf(stop ? 0.f : 0.5f * dn, &sh, &ch);
       const float4 dq = make_float4(ch, sh * d[0] * inv, sh * d[1] * inv, sh * d[2] * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const EvalH tr = eval_hess<G>(smem_tab, a.Lb, L, qt, qg, a.lbin);
+      const EvalH tr = eval_hess<G>(smem_tab, Lb, L, qt, qg, a.lbin);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -783,24 +820,27 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_wedge(const AlignA
                                                                     const float2* __restrict__ wt,
                                                                     const float2* __restrict__ ww) {
   extern __shared__ float4 smem_tab[];
-  float4* tabw = smem_tab + tab_base(a.Lb + 1, a.Lb);
   const int p = blockIdx.x;
+  __shared__ int sched[kMaxStages + 1];
+  load_schedule(a, p, sched);
+  const int Lb = sched[sched[0]];
+  float4* tabw = smem_tab + tab_base(Lb + 1, Lb);
   const int s = threadIdx.x / G, qg = threadIdx.x % G;
   const bool active = s < a.S;
   const int se = active ? s : s % a.S;
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, Lb, threadIdx.x,
               blockDim.x);
-  build_table(tabw, wlay, wt, ww, a.P, a.Lb, threadIdx.x, blockDim.x);
+  build_table(tabw, wlay, wt, ww, a.P, Lb, threadIdx.x, blockDim.x);
   __syncthreads();
   float4 q = qnormalize(a.starts[(size_t)p * a.S + se]);
   Eval cur;
   cur.S = 0.f;
   cur.gx = cur.gy = cur.gz = 0.f;
-  for (int st = 0; st < a.nstages; ++st) {
-    const int L = a.stages[st];
+  for (int st = 0; st < sched[0]; ++st) {
+    const int L = sched[1 + st];
     const float hmax = 3.14159265358979f / (float)L;
     float h = 0.5f * hmax;
-    cur = eval_constrained<G>(smem_tab, tabw, a.Lb, L, q, qg, a.lbin);
+    cur = eval_constrained<G>(smem_tab, tabw, Lb, L, q, qg, a.lbin);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -809,7 +849,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_wedge(const AlignA
       sincosf(stop ? 0.f : 0.5f * h, &sh, &ch);
       const float4 dq = make_float4(ch, sh * cur.gx * inv, sh * cur.gy * inv, sh * cur.gz * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const Eval tr = eval_constrained<G>(smem_tab, tabw, a.Lb, L, qt, qg, a.lbin);
+      const Eval tr = eval_constrained<G>(smem_tab, tabw, Lb, L, qt, qg, a.lbin);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -845,11 +885,14 @@ template <int G, int C, int NT>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs a) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
+  __shared__ int sched[kMaxStages + 1];
+  load_schedule(a, p, sched);
+  const int Lb = sched[sched[0]];
   const int chunk = threadIdx.x / G, qg = threadIdx.x % G;
   const int nchunks = a.S / C;
   const bool active = chunk < nchunks;
   const int ce = active ? chunk : chunk % nchunks;
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, Lb, threadIdx.x,
               blockDim.x);
   __syncthreads();
   float4 q[C];
@@ -860,12 +903,12 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs 
     q[j] = qnormalize(a.starts[(size_t)p * a.S + ce * C + j]);
     cur[j].S = cur[j].gx = cur[j].gy = cur[j].gz = 0.f;
   }
-  for (int st = 0; st < a.nstages; ++st) {
-    const int L = a.stages[st];
+  for (int st = 0; st < sched[0]; ++st) {
+    const int L = sched[1 + st];
     const float hmax = 3.14159265358979f / (float)L;
 #pragma unroll
     for (int j = 0; j < C; ++j) h[j] = 0.5f * hmax;
-    eval_rotations<G, C>(smem_tab, nullptr, a.Lb, L, q, qg, a.lbin, cur);
+    eval_rotations<G, C>(smem_tab, nullptr, Lb, L, q, qg, a.lbin, cur);
     for (int t = 0; t < a.steps; ++t) {
       float4 qt[C];
       bool stop[C];
@@ -880,7 +923,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs 
         qt[j] = qnormalize(qmul(q[j], dq));
       }
       Eval tr[C];
-      eval_rotations<G, C>(smem_tab, nullptr, a.Lb, L, qt, qg, a.lbin, tr);
+      eval_rotations<G, C>(smem_tab, nullptr, Lb, L, qt, qg, a.lbin, tr);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         if (!stop[j]) {
@@ -952,6 +995,89 @@ __global__ void __launch_bounds__(256) k_energy(Layout lay, const float2* __rest
     __syncthreads();
   }
   if (threadIdx.x == 0) energy[(size_t)p * (L + 1) + l] = (float)red[0];
+}
+
+// ---------------------------------------------------------------------------- band choice (energy ratio)
+// Marching bands per subtomogram from the energy ratio of Fig. 1: E_l = sum_{m,m'} |xi^l_{mm'}|^2 for
+// l <= Lc (xi^l_{mm'} = sum_k conj(t_klm) f_klm' summed in FP32, |xi|^2 and the sums over (m, m') in FP64,
+// per-warp partial sums added in warp order, so the result does not depend on timing), then
+// Ratio(L) = sum_{l>L} E_l / sum_{l<=Lc} E_l and band j = the smallest L >= L_min with Ratio(L) <= tau_j;
+// a band equal to the previous one is written once.  One CTA per subtomogram.
+struct BandRule {
+  int n;                    // thresholds, 1..kMaxStages
+  int L_min;                // lowest band, >= 1
+  double tau[kMaxStages];   // decreasing
+};
+
+constexpr int kBandThreads = 256;
+
+__global__ void __launch_bounds__(kBandThreads) k_choose_bands(Layout lay, const float2* __restrict__ tmpl,
+                                                               const int* __restrict__ tmpl_index, int n_templates,
+                                                               const float2* __restrict__ sub, int Lc, BandRule rule,
+                                                               int* __restrict__ stage_table,
+                                                               float* __restrict__ energy_out) {
+  __shared__ double part[kBandThreads / 32][kMaxL + 1];
+  const int p = blockIdx.x;
+  const float2* t = tmpl;
+  if (tmpl_index) {
+    int ti = tmpl_index[p];
+    ti = ti < 0 ? 0 : (ti >= n_templates ? n_templates - 1 : ti);
+    t += (size_t)ti * lay.Nb;
+  }
+  const float2* f = sub + (size_t)p * lay.Nb;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int l = 0; l <= Lc; ++l) {
+    const int w = 2 * l + 1, K = lay.K[l], off = lay.off[l];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < w * w; i += kBandThreads) {
+      const int m = i / w, n = i % w;
+      float xr = 0.f, xi = 0.f;
+      for (int k = 0; k < K; ++k) {
+        const float2 a = __ldg(t + off + k * w + m), b = __ldg(f + off + k * w + n);
+        xr = fmaf(a.x, b.x, fmaf(a.y, b.y, xr));
+        xi = fmaf(a.x, b.y, fmaf(-a.y, b.x, xi));
+      }
+      acc += (double)xr * xr + (double)xi * xi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[warp][l] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double E[kMaxL + 1];
+    double tot = 0.0;
+    for (int l = 0; l <= Lc; ++l) {
+      double e = 0.0;
+      for (int v = 0; v < kBandThreads / 32; ++v) e += part[v][l];
+      E[l] = e;
+      tot += e;
+      if (energy_out) energy_out[(size_t)p * (Lc + 1) + l] = (float)e;
+    }
+    // Ratio(L) = sum_{l>L} E_l / total, the tail summed from the highest degree down
+    double ratio[kMaxL + 1];
+    double tail = 0.0;
+    ratio[Lc] = 0.0;
+    for (int L = Lc - 1; L >= 0; --L) {
+      tail += E[L + 1];
+      ratio[L] = tot > 0.0 ? tail / tot : 0.0;
+    }
+    int* row = stage_table + (size_t)p * (kMaxStages + 1);
+    int n = 0, last = 0;
+    for (int j = 0; j < rule.n; ++j) {
+      int Lj = Lc;  // Ratio(Lc) = 0 always qualifies
+      for (int L = rule.L_min; L <= Lc; ++L)
+        if (ratio[L] <= rule.tau[j]) {
+          Lj = L;
+          break;
+        }
+      if (Lj > last) {
+        row[1 + n++] = Lj;
+        last = Lj;
+      }
+    }
+    row[0] = n;
+  }
 }
 
 // ---------------------------------------------------------------------------- FP64 re-scoring
@@ -1054,17 +1180,23 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
 constexpr int kMaxRefine = 64;
 
 template <int NL>
-__global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, int K, const double2* coef64,
+__global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int Lmax_band, int K, const double2* coef64,
                                                      const double* lbin64) {
   extern __shared__ float4 smem_tab[];
   __shared__ int top[kMaxRefine];
   __shared__ double part[kMaxRefine];  // [start][warp of the start] partial sums; K * max(1, NL/32) <= 64
   constexpr int W = NL > 32 ? NL / 32 : 1;
   const int p = blockIdx.x;
-  const int ntab = tab_base(a.Lb + 1, a.Lb);
+  // the band of the re-score: the subtomogram's last marching band with a per-subtomogram schedule, else
+  // the launch's band
+  __shared__ int sched[kMaxStages + 1];
+  load_schedule(a, p, sched);
+  const int L = a.stage_table ? sched[sched[0]] : Lmax_band;
+  const int Lb = L;
+  const int ntab = tab_base(Lb + 1, Lb);
   double2* Apow = reinterpret_cast<double2*>(smem_tab + ntab);
   double2* Bpow = Apow + (size_t)K * NL;
-  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, a.Lb, threadIdx.x,
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, Lb, threadIdx.x,
               blockDim.x);
   if (threadIdx.x == 0) {
     const float* sc = a.start_score_out + (size_t)p * a.S;
@@ -1090,7 +1222,7 @@ __global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, i
     Bpow[(size_t)s * NL + q] = make_double2(Bp.x, Bp.y);
   }
   __syncthreads();
-  const double S = score_rotation64<NL>(smem_tab, a.Lb, L, r, q, Apow + (size_t)se * NL, Bpow + (size_t)se * NL,
+  const double S = score_rotation64<NL>(smem_tab, Lb, L, r, q, Apow + (size_t)se * NL, Bpow + (size_t)se * NL,
                                         coef64, lbin64, a.lay.Lmax);
   if (active && (q & 31) == 0) part[s * W + q / 32] = S;
   __syncthreads();
@@ -1113,20 +1245,9 @@ __global__ void __launch_bounds__(512, 1) k_refine64(const AlignArgs a, int L, i
 
 size_t table_bytes(int Lb) { return (size_t)tab_base(Lb + 1, Lb) * sizeof(float4); }
 
-// Raise a kernel's dynamic shared-memory limit only when a larger size is requested, so that launches
-// recorded into a CUDA graph after a first (warm-up) call make no attribute calls.
-template <typename K>
-int ensure_smem(K kernel, std::atomic<int>& have, size_t smem) {
-  if ((int)smem <= have.load()) return BH_OK;
-  BH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  BH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  have.store((int)smem);
-  return BH_OK;
-}
-
 template <int G, int NT>
 int launch_align_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
-  static std::atomic<int> have{0};
+  static SmemAttr have;
   int st = ensure_smem(k_align<G, NT>, have, smem);
   if (st != BH_OK) return st;
   k_align<G, NT><<<a.B, NT, smem, stream>>>(a);
@@ -1141,7 +1262,7 @@ int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stre
   const size_t smem = std::max(table_bytes(a.Lb), score_only ? (size_t)16 : sel);
   if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
   if (score_only) {
-    static std::atomic<int> have{0};
+    static SmemAttr have;
     int st = ensure_smem(k_score<G>, have, smem);
     if (st != BH_OK) return st;
     k_score<G><<<a.B, threads, smem, stream>>>(a, L);
@@ -1163,7 +1284,7 @@ int launch_align_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stre
 
 template <int G, int NT>
 int launch_align_c2_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
-  static std::atomic<int> have{0};
+  static SmemAttr have;
   int st = ensure_smem(k_align_c<G, 2, NT>, have, smem);
   if (st != BH_OK) return st;
   k_align_c<G, 2, NT><<<a.B, NT, smem, stream>>>(a);
@@ -1215,7 +1336,7 @@ int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t
 
 template <int G, int NT>
 int launch_newton_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
-  static std::atomic<int> have{0};
+  static SmemAttr have;
   int st = ensure_smem(k_newton<G, NT>, have, smem);
   if (st != BH_OK) return st;
   k_newton<G, NT><<<a.B, NT, smem, stream>>>(a);
@@ -1230,7 +1351,7 @@ int launch_newton_g(const AlignArgs& a, bool score_only, int L, cudaStream_t str
   const size_t smem = std::max(table_bytes(a.Lb), score_only ? (size_t)16 : sel);
   if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
   if (score_only) {
-    static std::atomic<int> have{0};
+    static SmemAttr have;
     int st = ensure_smem(k_score_hess<G>, have, smem);
     if (st != BH_OK) return st;
     k_score_hess<G><<<a.B, threads, smem, stream>>>(a, L);
@@ -1265,7 +1386,7 @@ int launch_newton(const AlignArgs& a, int G, bool score_only, int L, cudaStream_
 
 template <int G, int NT>
 int launch_wedge_nt(const AlignArgs& a, const bh_wedge* w, size_t smem, cudaStream_t stream) {
-  static std::atomic<int> have{0};
+  static SmemAttr have;
   int st = ensure_smem(k_align_wedge<G, NT>, have, smem);
   if (st != BH_OK) return st;
   k_align_wedge<G, NT><<<a.B, NT, smem, stream>>>(a, w->layout, w->d_t, w->d_w);
@@ -1309,7 +1430,7 @@ int launch_refine_nl(const AlignArgs& a, int L, int K, const bh_plan* p, cudaStr
   const int threads = round_up(K * NL, 32);
   const size_t smem = table_bytes(a.Lb) + 2 * (size_t)K * NL * sizeof(double2);
   if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "FP64 re-score for band %d needs %zu B of shared memory", a.Lb, smem);
-  static std::atomic<int> have{0};
+  static SmemAttr have;
   int st = ensure_smem(k_refine64<NL>, have, smem);
   if (st != BH_OK) return st;
   k_refine64<NL><<<a.B, threads, smem, stream>>>(a, L, K, p->d_coef64, p->d_lbin64);
@@ -1388,7 +1509,7 @@ static int check_common(const bh_plan* p, const float* tmpl, const float* sub, i
   if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
   if (S < 1 || S > kMaxThreads) return fail(BH_ERR_ARG, "S=%d outside 1..%d", S, kMaxThreads);
   if (B > 0 && (!tmpl || !sub || !quats)) return fail(BH_ERR_ARG, "NULL input array");
-  return BH_OK;
+  return check_plan_device(p);
 }
 
 extern "C" int bh_score_grad(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* quats, int S,
@@ -1450,6 +1571,7 @@ extern "C" int bh_wedge_norm(const bh_plan* p, const bh_wedge* w, const float* q
   if (L < 0 || L > w->L) return fail(BH_ERR_ARG, "L=%d outside 0..%d (wedge band)", L, w->L);
   if (w->layout.Lmax != p->Lmax) return fail(BH_ERR_ARG, "wedge prepared for another plan");
   if (!quats || !dn) return fail(BH_ERR_ARG, "NULL array");
+  if (int st = check_plan_device(p); st != BH_OK) return st;
   AlignArgs a{};
   a.lay = w->layout;
   a.tmpl = w->d_t;
@@ -1504,6 +1626,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     }
     a.start_quat_out = reinterpret_cast<float4*>(opts->start_quat_out);
     a.start_score_out = opts->start_score_out;
+    a.stage_table = opts->stage_table;
     G = opts->group;
     C = opts->starts_per_thread;
     if (C < 0 || C > 2) return fail(BH_ERR_ARG, "starts_per_thread=%d not in {0,1,2}", C);
@@ -1555,6 +1678,41 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   return launch_refine(a, a.Lb, std::min(opts->refine_fp64, S), p, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int bh_refine_fp64(const bh_plan* p, const float* tmpl, const float* sub, int B, const float* start_quat,
+                              const float* start_score, int S, int L, int K, const int* tmpl_index, int n_templates,
+                              const int* stage_table, float* quat_out, float* score_out, double* score64_out,
+                              void* stream) {
+  clear_error();
+  const bh::Range range_("bh_refine_fp64");
+  int st = check_common(p, tmpl, sub, B, start_quat, S);
+  if (st != BH_OK) return st;
+  if (L < (stage_table ? 1 : 0) || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 0..%d", L, p->Lmax);
+  if (K < 1 || K > kMaxRefine || K > S) return fail(BH_ERR_ARG, "K=%d outside 1..min(%d, S=%d)", K, kMaxRefine, S);
+  if (tmpl_index && n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d with tmpl_index", n_templates);
+  if (B == 0) return BH_OK;
+  if (!start_score || !quat_out || !score_out) return fail(BH_ERR_ARG, "NULL array");
+  AlignArgs a{};
+  a.lay = p->layout;
+  a.tmpl = reinterpret_cast<const float2*>(tmpl);
+  a.sub = reinterpret_cast<const float2*>(sub);
+  a.tmpl_index = tmpl_index;
+  a.n_templates = tmpl_index ? n_templates : 0;
+  a.B = B;
+  a.S = S;
+  a.Lb = L;
+  a.nstages = 1;  // the band of subtomograms whose table row is empty
+  a.stages[0] = L;
+  a.stage_table = stage_table;
+  a.P = p->d_P;
+  a.lbin = p->d_lbin;
+  a.start_quat_out = reinterpret_cast<float4*>(const_cast<float*>(start_quat));
+  a.start_score_out = const_cast<float*>(start_score);
+  a.quat_out = reinterpret_cast<float4*>(quat_out);
+  a.score_out = score_out;
+  a.score64_out = score64_out;
+  return launch_refine(a, L, K, p, static_cast<cudaStream_t>(stream));
+}
+
 extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out) {
   clear_error();
   const bh::Range range_("bh_autotune");
@@ -1564,6 +1722,7 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
   if (!stages || nstages < 1 || nstages > kMaxStages) return fail(BH_ERR_ARG, "nstages=%d", nstages);
   const int Lb = stages[nstages - 1];
   if (Lb < 1 || Lb > p->Lmax) return fail(BH_ERR_ARG, "band %d", Lb);
+  if (int rc = check_plan_device(p); rc != BH_OK) return rc;
   cudaStream_t st;
   BH_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   cudaEvent_t e0, e1;
@@ -1628,7 +1787,7 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
   p->align_group[{Lb, S}] = {best_g, best_c};
   int best_bn = 0;
   float best_ems = 0.f;
-  if (p->mode == BH_MODE_BF16_SPLIT) {
+  if (p->mode == BH_MODE_BF16_SPLIT && !p->match_only) {
     AT_TRY(cudaMalloc(&vols, (size_t)B * N3 * 4));
     AT_TRY(cudaMemsetAsync(vols, 0x3C, (size_t)B * N3 * 4, st));
     best_ems = 1e30f;
@@ -1676,6 +1835,7 @@ extern "C" int bh_autotune_newton(bh_plan* p, int B, int S, const int* stages, i
   if (!stages || nstages < 1 || nstages > kMaxStages) return fail(BH_ERR_ARG, "nstages=%d", nstages);
   const int Lb = stages[nstages - 1];
   if (Lb < 1 || Lb > p->Lmax) return fail(BH_ERR_ARG, "band %d", Lb);
+  if (int rc = check_plan_device(p); rc != BH_OK) return rc;
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float *coef = nullptr, *tmpl = nullptr, *starts = nullptr, *quat = nullptr, *score = nullptr;
@@ -1749,6 +1909,7 @@ extern "C" int bh_energy(const bh_plan* p, const float* tmpl, const float* sub, 
   if (B == 0) return BH_OK;
   if (!tmpl || !sub || !energy) return fail(BH_ERR_ARG, "NULL array");
   if (tmpl_index && n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d", n_templates);
+  if (int st = check_plan_device(p); st != BH_OK) return st;
   if (B > 65535 * 1024) return fail(BH_ERR_ARG, "B=%d too large", B);
   dim3 grid(B, L + 1);
   k_energy<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(p->layout, reinterpret_cast<const float2*>(tmpl),
@@ -1786,6 +1947,36 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 }  // namespace bh
 
+extern "C" int bh_choose_bands(const bh_plan* p, const float* tmpl, const float* sub, int B, int L,
+                               const int* tmpl_index, int n_templates, const double* thresholds, int n_thresholds,
+                               int L_min, int* stage_table, float* energy, void* stream) {
+  clear_error();
+  const bh::Range range_("bh_choose_bands");
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (B < 0 || L < 1 || L > p->Lmax) return fail(BH_ERR_ARG, "B=%d L=%d (band 1..%d)", B, L, p->Lmax);
+  if (!thresholds || n_thresholds < 1 || n_thresholds > kMaxStages)
+    return fail(BH_ERR_ARG, "n_thresholds=%d outside 1..%d", n_thresholds, kMaxStages);
+  if (L_min < 1 || L_min > L) return fail(BH_ERR_ARG, "L_min=%d outside 1..%d", L_min, L);
+  BandRule rule{};
+  rule.n = n_thresholds;
+  rule.L_min = L_min;
+  for (int j = 0; j < n_thresholds; ++j) {
+    const double t = thresholds[j];
+    if (!(t > 0.0 && t < 1.0)) return fail(BH_ERR_ARG, "threshold %d = %g outside (0, 1)", j, t);
+    if (j > 0 && !(t < thresholds[j - 1])) return fail(BH_ERR_ARG, "thresholds must decrease");
+    rule.tau[j] = t;
+  }
+  if (tmpl_index && n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d", n_templates);
+  if (int st = check_plan_device(p); st != BH_OK) return st;
+  if (B == 0) return BH_OK;
+  if (!tmpl || !sub || !stage_table) return fail(BH_ERR_ARG, "NULL array");
+  k_choose_bands<<<B, kBandThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      p->layout, reinterpret_cast<const float2*>(tmpl), tmpl_index, n_templates, reinterpret_cast<const float2*>(sub),
+      L, rule, stage_table, energy);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
 extern "C" size_t bh_align_shifts_workspace(const bh_plan* p, int B, int nshift, int S) {
   if (!p || B < 0 || nshift < 1 || S < 1) return 0;
   const size_t R = (size_t)B * nshift;
@@ -1801,6 +1992,8 @@ extern "C" int bh_align_shifts(bh_plan* p, const float* tmpl, const float* vols,
   const bh::Range range_("bh_align_shifts");
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
   if (B < 0 || nshift < 1 || nshift > 4096 || S < 1) return fail(BH_ERR_ARG, "B=%d nshift=%d S=%d", B, nshift, S);
+  if (int st = check_plan_device(p); st != BH_OK) return st;
+  if (int st = check_expansion_plan(p); st != BH_OK) return st;
   if (B == 0) return BH_OK;
   if (!tmpl || !vols || !shifts || !starts || !workspace || !shift_out || !quat_out || !score_out)
     return fail(BH_ERR_ARG, "NULL argument");
@@ -2213,6 +2406,7 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
   if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
   if (L < 1 || L > p->Lmax) return fail(BH_ERR_ARG, "L=%d outside 1..%d", L, p->Lmax);
   if (S < 1 || S > grid->n) return fail(BH_ERR_ARG, "S=%d outside 1..%d (grid size)", S, grid->n);
+  if (int st = check_plan_device(p); st != BH_OK) return st;
   if (tmpl_index && n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d with tmpl_index", n_templates);
   if (B == 0) return BH_OK;
   if (!tmpl || !sub || !starts_out) return fail(BH_ERR_ARG, "NULL array");
@@ -2278,7 +2472,7 @@ extern "C" int bh_candidates(const bh_plan* p, const bh_grid* grid, const float*
     GridArgs g{grid->d_q, grid->n, grid->npow2, L,
                reinterpret_cast<float4*>(starts_out), index_out, grid_score_out, scores, n_pad,
                grid->d_pairs, grid->n_pairs};
-    static std::atomic<int> have{0};
+    static SmemAttr have;
     st = ensure_smem(k_grid_candidates, have, smem);
     if (st == BH_OK) {
       k_grid_candidates<<<B, kCandThreads, smem, cs>>>(a, g);

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -49,6 +50,34 @@ void legendre_all(int L, double x, double* P);
   } while (0)
 
 constexpr int kMaxL = 64;
+constexpr int kMaxDevices = 128;
+
+// Ordinal of the current CUDA device in *dev (BH_ERR_CUDA if the runtime cannot say, BH_ERR_UNSUPPORTED
+// beyond kMaxDevices).
+inline int current_device(int* dev) {
+  BH_CUDA_TRY(cudaGetDevice(dev));
+  if (*dev < 0 || *dev >= kMaxDevices) return fail(BH_ERR_UNSUPPORTED, "device ordinal %d", *dev);
+  return BH_OK;
+}
+
+// Kernel attributes set by cudaFuncSetAttribute belong to the device that was current at the call, so the
+// record of what was already raised is kept per device.  ensure_smem raises a kernel's dynamic shared-memory
+// limit only when a larger size is requested on this device, so that launches recorded into a CUDA graph
+// after a first (warm-up) call make no attribute calls.
+struct SmemAttr {
+  std::atomic<int> have[kMaxDevices] = {};
+};
+template <typename K>
+int ensure_smem(K kernel, SmemAttr& attr, size_t smem) {
+  int dev = 0;
+  const int st = current_device(&dev);
+  if (st != BH_OK) return st;
+  if ((int)smem <= attr.have[dev].load()) return BH_OK;
+  BH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BH_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  attr.have[dev].store((int)smem);
+  return BH_OK;
+}
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 inline int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -72,6 +101,7 @@ constexpr int kPadNb = 256;  // Nb is padded to a multiple of 256 (FP32 and tens
 struct bh_plan {
   int device = -1;
   int N = 0, Lmax = 0, mode = 0, max_batch = 0;
+  bool match_only = false;          // BH_PLAN_MATCH_ONLY: no expansion table or scratch
   double lam_max = 0;
   int V = 0, V_pad = 0, Nb = 0, Nb_pad = 0, M_cap = 0;
   std::vector<int> K, offs;         // per degree
@@ -101,6 +131,20 @@ struct bh_plan {
 };
 
 namespace bh {
+// A plan's tables live on the device it was created on; calls that read them must run with that device
+// current (BH_ERR_ARG otherwise, before anything is enqueued).
+inline int check_plan_device(const bh_plan* p) {
+  int dev = 0;
+  const int st = current_device(&dev);
+  if (st != BH_OK) return st;
+  if (dev != p->device) return fail(BH_ERR_ARG, "plan lives on device %d, current device is %d", p->device, dev);
+  return BH_OK;
+}
+// Calls that expand volumes need the plan's basis table.
+inline int check_expansion_plan(const bh_plan* p) {
+  if (p->match_only) return fail(BH_ERR_ARG, "the plan was created with BH_PLAN_MATCH_ONLY (no expansion table)");
+  return BH_OK;
+}
 // expand.cu
 int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const std::vector<double>& angular,
                  const std::vector<int>& vox_r2, const std::vector<int2>& colinfo, double h3);

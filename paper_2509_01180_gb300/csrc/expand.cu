@@ -638,11 +638,9 @@ static int launch_to_complex(const bh_plan* p, const float* C, int rows, float* 
                              cudaStream_t stream) {
   const size_t row_bytes = (size_t)p->Nb_pad * sizeof(float);
   if (row_bytes <= 96 * 1024) {
-    static bool attr = false;
-    if (!attr) {
-      BH_CUDA_TRY(cudaFuncSetAttribute(k_to_complex_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-      attr = true;
-    }
+    static SmemAttr attr;
+    const int st = ensure_smem(k_to_complex_rows, attr, 96 * 1024);
+    if (st != BH_OK) return st;
     k_to_complex_rows<<<rows, 256, row_bytes, stream>>>(C, p->Nb_pad, p->Nb, p->d_slot, reinterpret_cast<float2*>(coeffs),
                                                         splits, stride);
   } else {
@@ -665,12 +663,9 @@ static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
   }
   const int num_kb = p->V_pad / kGemmBK;
   const int kb_split = round_up((num_kb + splits - 1) / splits, KCHUNK);
-  static bool attr = false;
-  if (!attr) {
-    BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_promoted, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)PCfg::SMEM));
-    attr = true;
-  }
+  static SmemAttr attr;
+  const int st = ensure_smem(k_gemm_tc_promoted, attr, PCfg::SMEM);
+  if (st != BH_OK) return st;
   dim3 grid(Mp / kGemmBM, p->Nb_pad / PBN, (num_kb + kb_split - 1) / kb_split);
   k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
                                                       p->Nb_pad, num_kb, kb_split, stride, p->d_err);
@@ -712,8 +707,9 @@ int expand_into(bh_plan* p, const float* vols, const float* const* vptr, int B, 
       k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, scratch_c, Mp, p->Nb_pad, p->V_pad, p->V_pad, 0);
     } else {
       const int num_kb = p->V_pad / kGemmBK;
-      BH_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_promoted, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PCfg::SMEM));
+      static SmemAttr attr;
+      const int st = ensure_smem(k_gemm_tc_promoted, attr, PCfg::SMEM);
+      if (st != BH_OK) return st;
       dim3 grid(Mp / kGemmBM, p->Nb_pad / PBN);
       k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c, p->Nb_pad,
                                                           num_kb, num_kb, 0, p->d_err);
@@ -786,6 +782,10 @@ extern "C" int bh_plan_status(bh_plan* p) {
 extern "C" int bh_plan_probe_wait(bh_plan* p, void* stream) {
   clear_error();
   if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  {
+    const int st = check_plan_device(p);
+    if (st != BH_OK) return st;
+  }
   bh::k_wait_probe<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(p->d_err, 199);
   BH_CHECK_LAUNCH();
   return BH_OK;
@@ -798,6 +798,11 @@ extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, vo
   if (B < 0) return fail(BH_ERR_ARG, "B=%d", B);
   if (B == 0) return BH_OK;
   if (!vols || !coeffs) return fail(BH_ERR_ARG, "vols or coeffs is NULL");
+  {
+    int st = check_plan_device(p);
+    if (st == BH_OK) st = check_expansion_plan(p);
+    if (st != BH_OK) return st;
+  }
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const long long N3 = (long long)p->N * p->N * p->N;
   for (int b0 = 0; b0 < B; b0 += p->max_batch) {

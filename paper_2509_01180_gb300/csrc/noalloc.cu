@@ -53,6 +53,13 @@ extern "C" int bh_expand_noalloc(bh_plan* p, const float* vols, int B, float* co
   if (B < 0) return bh::fail(BH_ERR_ARG, "B=%d", B);
   if (B == 0) return BH_OK;
   if (!vols || !coeffs) return bh::fail(BH_ERR_ARG, "vols or coeffs is NULL");
+  // the plan's tables and tensor maps live on its own device; the scratch looked up below must be that
+  // device's copy of the array
+  {
+    int st = bh::check_plan_device(p);
+    if (st == BH_OK) st = bh::check_expansion_plan(p);
+    if (st != BH_OK) return st;
+  }
   // bytes per row of the 128-row M tile: gathered volume (FP32, or BF16 hi + lo) + real GEMM output (FP32)
   const size_t row_bytes = (size_t)p->V_pad * 4 + (size_t)p->Nb_pad * 4;
   const size_t tile_rows = bh::kGemmBM;

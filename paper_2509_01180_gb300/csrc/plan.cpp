@@ -225,6 +225,8 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   if (lam_max > 1e4) return fail(BH_ERR_ARG, "lambda_max %g too large", lam_max);
   const int max_batch = (o->max_batch > 0) ? o->max_batch : 512;
   if (max_batch > (1 << 20)) return fail(BH_ERR_ARG, "max_batch %d too large", max_batch);
+  if (o->flags & ~BH_PLAN_MATCH_ONLY) return fail(BH_ERR_ARG, "flags=%d", o->flags);
+  const bool match_only = (o->flags & BH_PLAN_MATCH_ONLY) != 0;
 
   int dev = 0;
   BH_CUDA_TRY(cudaGetDevice(&dev));
@@ -243,6 +245,7 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   p->mode = o->mode;
   p->max_batch = max_batch;
   p->lam_max = lam_max;
+  p->match_only = match_only;
 
   // ---- index set (FP64 roots and constants)
   compute_roots(p->Lmax, lam_max, p->K, p->lam, p->cst);
@@ -280,8 +283,8 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   p->Nb_pad = round_up(p->Nb, kPadNb);
   p->M_cap = round_up(max_batch, kGemmBM);
 
-  // ---- radial table R[lk][r2] = c_lk j_l(lambda_lk sqrt(r2)/h), r2 = 0..h^2-1
-  const int n_r2 = h * h;
+  // ---- radial table R[lk][r2] = c_lk j_l(lambda_lk sqrt(r2)/h), r2 = 0..h^2-1 (expansion plans only)
+  const int n_r2 = match_only ? 0 : h * h;
   int nlk = 0;
   for (int l = 0; l <= p->Lmax; ++l) nlk += p->K[l];
   std::vector<double> radial((size_t)nlk * n_r2);
@@ -308,8 +311,8 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
 
   // ---- angular table A[lm][v], lm = l^2 + l + m (real form, see header comment)
   const int nlm = (p->Lmax + 1) * (p->Lmax + 1);
-  std::vector<double> angular((size_t)nlm * p->V);
-  {
+  std::vector<double> angular(match_only ? 0 : (size_t)nlm * p->V);
+  if (!match_only) {
     std::vector<std::thread> th;
     const int nth = std::max(1u, std::thread::hardware_concurrency());
     const int L = p->Lmax;
@@ -387,7 +390,9 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   PLAN_TRY(cuda_ok(cudaMemset(p->d_err, 0, sizeof(int)), "memset err"));
   const size_t tab_elems = (size_t)p->Nb_pad * p->V_pad;
   const size_t x_elems = (size_t)p->M_cap * p->V_pad;
-  if (p->mode == BH_MODE_FP32) {
+  if (match_only) {
+    // no table, gathered volumes or GEMM output
+  } else if (p->mode == BH_MODE_FP32) {
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_T32, sizeof(float) * tab_elems), "cudaMalloc table"));
     PLAN_TRY(cuda_ok(cudaMalloc(&p->d_X32, sizeof(float) * x_elems), "cudaMalloc X"));
   } else {
@@ -402,7 +407,9 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     const int tiles = p->Nb_pad / 128;
     p->ksplit_max = std::max(1, std::min(8, (2 * p->num_sms + tiles - 1) / tiles));
   }
-  PLAN_TRY(cuda_ok(cudaMalloc(&p->d_C, sizeof(float) * (size_t)p->ksplit_max * p->M_cap * p->Nb_pad), "cudaMalloc C"));
+  if (!match_only)
+    PLAN_TRY(cuda_ok(cudaMalloc(&p->d_C, sizeof(float) * (size_t)p->ksplit_max * p->M_cap * p->Nb_pad),
+                     "cudaMalloc C"));
   // ---- scale of the rescaled Wigner-d recursion: P_l(m,n) = prod_{j=m+1..l} j(2j-1)/sqrt((j^2-m^2)(j^2-n^2)),
   //      rows m = 0..Lmax, each [l = m..Lmax][n = -m..m]
   {
@@ -455,8 +462,10 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
                      "upload lbin64"));
   }
   const double hv = 2.0 / N;
-  PLAN_TRY(upload_table(p, radial, n_r2, angular, vox_r2, colinfo, hv * hv * hv));
-  if (p->mode == BH_MODE_BF16_SPLIT) PLAN_TRY(make_tensor_maps(p));
+  if (!match_only) {
+    PLAN_TRY(upload_table(p, radial, n_r2, angular, vox_r2, colinfo, hv * hv * hv));
+    if (p->mode == BH_MODE_BF16_SPLIT) PLAN_TRY(make_tensor_maps(p));
+  }
   PLAN_TRY(cuda_ok(cudaDeviceSynchronize(), "plan build"));
 #undef PLAN_TRY
   *out = p;
@@ -489,5 +498,6 @@ extern "C" int bh_plan_info(const bh_plan* p, bh_plan_opts* o) {
   o->lambda_max = p->lam_max;
   o->mode = p->mode;
   o->max_batch = p->max_batch;
+  o->flags = p->match_only ? BH_PLAN_MATCH_ONLY : 0;
   return BH_OK;
 }

@@ -155,25 +155,62 @@ CONFIGS = {
 }
 
 
+def _workload_particle(tpl: BlobTemplate, N: int, p: int, master: int, snr, wedge):
+    """Ground-truth rotation and degraded volume of particle p (its own seeded generator)."""
+    rng = rng_for(2, p, master)
+    q = uniform_quaternions(rng, 1)[0]
+    return q, degrade(render(N, tpl, q), rng, snr, wedge)
+
+
+def _workload_chunk(job):
+    """Worker (spawned process): rotations and volumes of particles lo..hi-1 of a workload."""
+    count, name, first, lo, hi, master, snr, wedge, dtype = job
+    N, _, nb, sigma = CONFIGS[name][:4]
+    tpl = blob_template(rng_for(1, 0, master), nb, sigma, 0.75 * N / 2)
+    qs = np.empty((hi - lo, 4))
+    vols = np.empty((hi - lo, N, N, N), dtype=dtype)
+    for j in range(lo, hi):
+        qs[j - lo], v = _workload_particle(tpl, N, first + j, master, snr, wedge)
+        vols[j - lo] = v.astype(dtype)
+    return lo, qs, vols
+
+
+def _parallel_chunks(fn, jobs, workers: int):
+    """fn over jobs in a pool of `workers` spawned processes (results in job order)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(fn, jobs, chunksize=1)
+
+
+def _chunks(count: int, workers: int):
+    step = max(1, -(-count // (4 * workers)))
+    return [(lo, min(count, lo + step)) for lo in range(0, count, step)]
+
+
 def make_workload(name: str, count: int | None = None, first: int = 0, master: int = MASTER_SEED,
-                  snr=..., wedge=..., dtype=np.float32) -> Workload:
-    """Build particles first .. first+count-1 of a named workload (all deterministic in the seeds)."""
+                  snr=..., wedge=..., dtype=np.float32, workers: int = 1) -> Workload:
+    """Build particles first .. first+count-1 of a named workload (all deterministic in the seeds; the same
+    arrays whatever `workers`, the number of spawned processes that render the volumes)."""
     N, Lmax, nb, sigma, snr0, wedge0, stages, steps, S, B = CONFIGS[name]
     snr = snr0 if snr is ... else snr
     wedge = wedge0 if wedge is ... else wedge
     count = B if count is None else count
     tpl = blob_template(rng_for(1, 0, master), nb, sigma, 0.75 * N / 2)
     template = render(N, tpl).astype(dtype)
-    vols = np.empty((count, N, N, N), dtype=dtype)
     q_true = np.empty((count, 4))
     starts = np.empty((count, S, 4), dtype=np.float32)
+    vols = np.empty((count, N, N, N), dtype=dtype)
+    if workers > 1 and count > 1:
+        jobs = [(count, name, first, lo, hi, master, snr, wedge, np.dtype(dtype)) for lo, hi in _chunks(count, workers)]
+        for lo, qs, vs in _parallel_chunks(_workload_chunk, jobs, workers):
+            q_true[lo:lo + len(qs)] = qs
+            vols[lo:lo + len(qs)] = vs
+    else:
+        for j in range(count):
+            q_true[j], v = _workload_particle(tpl, N, first + j, master, snr, wedge)
+            vols[j] = v.astype(dtype)
     for j in range(count):
-        p = first + j
-        rng = rng_for(2, p, master)
-        q = uniform_quaternions(rng, 1)[0]
-        q_true[j] = q
-        vols[j] = degrade(render(N, tpl, q), rng, snr, wedge).astype(dtype)
-        starts[j] = uniform_quaternions(rng_for(3, p, master), S).astype(np.float32)
+        starts[j] = uniform_quaternions(rng_for(3, first + j, master), S).astype(np.float32)
     return Workload(name, N, Lmax, math.pi * N / 2, list(stages), steps, S, template, vols, q_true, starts,
                     {"blobs": nb, "sigma": sigma, "snr": snr, "wedge_deg": wedge, "first": first})
 
@@ -216,33 +253,65 @@ MIXED_CLASSES = [(24, 3000), (40, 2000), (64, 1000)]
 MIXED_BLOBS = [40, 93, 146, 200]
 
 
-def make_mixed(scale: float = 1.0, distinct: int | None = None, master: int = MASTER_SEED) -> list:
+def _mixed_class_templates(ci: int, N: int, master: int):
+    sigma = 1.2 + 0.8 * (N - 16) / 48
+    return [blob_template(rng_for(10 + ci, t, master), nb, sigma, 0.75 * N / 2) for t, nb in enumerate(MIXED_BLOBS)]
+
+
+def _mixed_particle(tpls, ci: int, N: int, j: int, master: int):
+    """Template index, rotation, start count and degraded volume of particle j of class ci."""
+    rng = rng_for(20 + ci, j, master)
+    t = int(rng.integers(0, len(tpls)))
+    q = uniform_quaternions(rng, 1)[0]
+    snr = rng.uniform(0.03, 0.2)
+    wedge = rng.uniform(50.0, 70.0)
+    vol = degrade(render(N, tpls[t], q), rng, snr, wedge)
+    S = (8, 16, 32)[rng.integers(0, 3)]
+    return t, q, S, vol
+
+
+def _mixed_chunk(job):
+    """Worker (spawned process): particles lo..hi-1 of one mixed class."""
+    ci, N, lo, hi, master = job
+    tpls = _mixed_class_templates(ci, N, master)
+    vols = np.empty((hi - lo, N, N, N), dtype=np.float32)
+    meta = []
+    for j in range(lo, hi):
+        t, q, S, v = _mixed_particle(tpls, ci, N, j, master)
+        vols[j - lo] = v.astype(np.float32)
+        meta.append((t, q, S))
+    return lo, meta, vols
+
+
+def make_mixed(scale: float = 1.0, distinct: int | None = None, master: int = MASTER_SEED, workers: int = 1) -> list:
     """Batched uneven workload: classes of 24^3 (l <= 12), 40^3 (l <= 20) and 64^3 (l <= 32) subtomograms,
     4 blob templates per class (40-200 blobs), SNR ~ U[0.03, 0.2], wedge half-angle ~ U[50, 70] deg,
     starts per particle ~ uniform on {8, 16, 32}, 30 steps per band.  `scale` multiplies the class
-    counts; with `distinct`, only that many particles per class are generated and the rest repeat them."""
+    counts; with `distinct`, only that many particles per class are generated and the rest repeat them.
+    `workers` > 1 renders the volumes in that many spawned processes (same arrays)."""
     out = []
     for ci, (N, count) in enumerate(MIXED_CLASSES):
         count = max(1, int(round(count * scale)))
         L = N // 2
-        sigma = 1.2 + 0.8 * (N - 16) / 48
-        tpls = [blob_template(rng_for(10 + ci, t, master), nb, sigma, 0.75 * N / 2) for t, nb in enumerate(MIXED_BLOBS)]
+        tpls = _mixed_class_templates(ci, N, master)
         templates = np.stack([render(N, t) for t in tpls]).astype(np.float32)
         n_gen = count if distinct is None else min(count, distinct)
-        vols = np.empty((n_gen, N, N, N), dtype=np.float32)
         tidx = np.empty(n_gen, dtype=np.int32)
         q_true = np.empty((n_gen, 4))
         S = np.empty(n_gen, dtype=np.int32)
         starts = np.zeros((n_gen, 32, 4), dtype=np.float32)
+        vols = np.empty((n_gen, N, N, N), dtype=np.float32)
+        if workers > 1 and n_gen > 1:
+            jobs = [(ci, N, lo, hi, master) for lo, hi in _chunks(n_gen, workers)]
+            for lo, meta, vs in _parallel_chunks(_mixed_chunk, jobs, workers):
+                vols[lo:lo + len(meta)] = vs
+                for i, (t, q, s_) in enumerate(meta):
+                    tidx[lo + i], q_true[lo + i], S[lo + i] = t, q, s_
+        else:
+            for j in range(n_gen):
+                tidx[j], q_true[j], S[j], v = _mixed_particle(tpls, ci, N, j, master)
+                vols[j] = v.astype(np.float32)
         for j in range(n_gen):
-            rng = rng_for(20 + ci, j, master)
-            tidx[j] = rng.integers(0, len(tpls))
-            q = uniform_quaternions(rng, 1)[0]
-            q_true[j] = q
-            snr = rng.uniform(0.03, 0.2)
-            wedge = rng.uniform(50.0, 70.0)
-            vols[j] = degrade(render(N, tpls[tidx[j]], q), rng, snr, wedge).astype(np.float32)
-            S[j] = (8, 16, 32)[rng.integers(0, 3)]
             starts[j, :S[j]] = uniform_quaternions(rng_for(30 + ci, j, master), S[j]).astype(np.float32)
         if n_gen < count:
             rep = np.arange(count) % n_gen

@@ -9,8 +9,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
+    # the 32^3 workload keeps this CPU test short; the default (64^3) takes the same code path
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                          "--warmup", "1", "--workload", "batch32"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
@@ -22,3 +24,16 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert "workload" in d["config"]
+
+
+def test_default_workload_is_the_precision_form():
+    """Without flags the bench measures the largest single-GPU configuration: 4096 x 64^3, l <= 32, marching
+    4-8-16-32, 32 starts, with the FP64 re-score of the best starts."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2509_01180_gb300 import synth
+    assert bench.HEADLINE == "precision64"
+    N, Lmax, _, _, _, _, stages, steps, S, B = synth.CONFIGS[bench.HEADLINE]
+    assert (N, Lmax, stages, steps, S, B) == (64, 32, [4, 8, 16, 32], 30, 32, 4096)
+    # flop accounting: one evaluation at band L costs 30 flop per orbit-step and 46 per orbit
+    assert bench.orbit_steps(32) == 12529 and bench.eval_flops(4) == 30 * 55 + 46 * 25

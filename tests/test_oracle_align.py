@@ -120,6 +120,25 @@ def test_energy_ratio():
     assert np.allclose(r, [34 / 35, 25 / 35, 0.0])
 
 
+def _xi_with_energies(e):
+    """xi^l with sum_{m,m'} |xi^l_{mm'}|^2 = e[l] (constant entries)."""
+    return [np.full((2 * l + 1, 2 * l + 1), math.sqrt(e[l]) / (2 * l + 1) + 0j) for l in range(len(e))]
+
+
+def test_band_choice_hand_example():
+    """Energies 8, 4, 2, 1, 1 over l = 0..4 (total 16): Ratio(L) = 8/16, 4/16, 2/16, 1/16, 0 for L = 0..4.
+    Thresholds 0.3, 0.1, 0.01: the first L with Ratio <= 0.3 is 1 (0.25), with <= 0.1 it is 3 (0.0625), with
+    <= 0.01 it is 4 (0).  A lowest band of 2 moves the first band to 2; thresholds that pick the same band
+    give it once."""
+    xi = _xi_with_energies([8.0, 4.0, 2.0, 1.0, 1.0])
+    assert np.allclose(align.energy_ratio(xi), [0.5, 0.25, 0.125, 0.0625, 0.0])
+    assert align.choose_bands(xi, [0.3, 0.1, 0.01]) == [1, 3, 4]
+    assert align.choose_bands(xi, [0.3, 0.1, 0.01], L_min=2) == [2, 3, 4]
+    assert align.choose_bands(xi, [0.3, 0.26, 0.2]) == [1, 2]
+    assert align.choose_bands(xi, [0.25, 0.0625]) == [1, 3]  # Ratio equal to the threshold qualifies
+    assert align.choose_bands(xi, [0.9]) == [1]  # bands start at 1 even when Ratio(0) is below tau
+
+
 def test_marching_on_noiseless_voxel_phantom():
     """Plain method, FP64, one noiseless 16^3 pair (l <= 8, 2-4-8, 8 starts, 50 steps): the recovered
     rotation is R_true^{-1} up to the voxelisation and truncation bias (reported, loosely gated)."""

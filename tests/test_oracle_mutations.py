@@ -154,3 +154,19 @@ def test_dft_power_pin_catches_mistakes(monkeypatch, old, new):
     from tests import test_oracle_wedge as twd
     monkeypatch.setattr(wedge, "dft_power", _mutant(wedge, "dft_power", old, new))
     assert _fails(twd.test_dft_power_is_the_direct_dft_of_the_ball_restricted_volume)
+
+
+# ---------------------------------------------------------------------------- band choice (Fig. 1, Sec. III)
+@pytest.mark.parametrize("old,new", [
+    ("if r[L] <= tau)", "if r[L] < tau)"),                      # strict comparison
+    ("range(L_min, Lmax + 1)", "range(0, Lmax + 1)"),           # band 0 allowed
+    ("if not bands or L > bands[-1]:", "if True:"),             # repeats kept
+    ("if r[L] <= tau)", "if 1.0 - r[L] <= tau)"),               # captured instead of remaining energy
+])
+def test_band_choice_pin_catches_mistakes(monkeypatch, old, new):
+    monkeypatch.setattr(align, "choose_bands", _mutant(align, "choose_bands", old, new))
+    try:
+        ta.test_band_choice_hand_example()
+    except (AssertionError, StopIteration):  # a wrong band, or no band found at all
+        return
+    raise AssertionError("the planted mistake passed the pin")
