@@ -300,11 +300,13 @@ def run_workload(args, w, rank, world, device, *, refine: int, sec3: bool, wedge
         plan_s = time.perf_counter() - t0
         progress(f"{w.name} {name}: plan {plan_s:.1f} s")
         if args.no_autotune:
-            tune = {"align_group": args.group, "align_starts_per_thread": args.starts_per_thread, "gemm_bn": 128}
+            tune = {"align_group": args.group, "align_starts_per_thread": args.starts_per_thread, "gemm_bn": 128,
+                    "align_dealing": args.dealing}
         else:
             tune = bh.bh_autotune(plan, B, w.S, w.stages, w.steps)  # picks kernel variants (untimed setup)
         grp = args.group if args.no_autotune else 0
         spt = args.starts_per_thread if args.no_autotune else 0
+        dea = args.dealing if args.no_autotune else 0
         tmpl = bh.bh_expand(plan, tvol)[0].contiguous()
         coeffs = torch.empty((B, plan.Nb, 2), dtype=torch.float32, device=device)
         quat = torch.empty((B, 4), dtype=torch.float32, device=device)
@@ -315,7 +317,7 @@ def run_workload(args, w, rank, world, device, *, refine: int, sec3: bool, wedge
         def ascend():
             if refine:  # per-start outputs feed the FP64 re-score of the best `refine` starts
                 o = bh.AlignOpts()
-                o.group, o.starts_per_thread = grp, spt
+                o.group, o.starts_per_thread, o.dealing = grp, spt, dea
                 o.start_quat_out, o.start_score_out = sq.data_ptr(), ss.data_ptr()
                 st = (bh.ctypes.c_int * len(w.stages))(*w.stages)
                 bh._check(bh.lib().bh_align_batch(plan.handle, tmpl.data_ptr(), coeffs.data_ptr(), B,
@@ -324,7 +326,7 @@ def run_workload(args, w, rank, world, device, *, refine: int, sec3: bool, wedge
                                                   stream.cuda_stream), "bh_align_batch")
             else:
                 bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
-                                  stream=stream, group=grp, starts_per_thread=spt)
+                                  stream=stream, group=grp, starts_per_thread=spt, dealing=dea)
 
         def rescore():
             if refine:
@@ -408,7 +410,8 @@ def run_workload(args, w, rank, world, device, *, refine: int, sec3: bool, wedge
             name == "bf16split" and args.band_leg) else None
         results[name] = {"refine": refine, "wedge": wedge_res, "sec3": sec3_res, "bands": band_res, "plan_s": plan_s, "tune": tune, "t_tot": t_tot,
                          "t_exp": t_exp, "t_aln": t_aln, "t_ref": t_ref, "q": q_res, "clocks": clk.summary(),
-                         "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V, "passes": -(-B // plan.max_batch),
+                         "e2e_ms": e2e_ms, "Nb": plan.Nb, "V": plan.V, "gemm_K": plan.gemm_K, "gemm_N": plan.gemm_N,
+                         "passes": -(-B // plan.max_batch),
                          "h2d": int(hv.numel() * 4), "d2h": int(hq[0].numel() * 4 + hs[0].numel() * 4)}
         plan.destroy()
         del coeffs, hv
@@ -429,23 +432,31 @@ def summarize(args, w, res, world, device) -> dict:
     peaks = measured_peaks()
     per = {"expand": r["t_exp"] / steps, "align": r["t_aln"] / steps, "rescore_fp64": r["t_ref"] / steps}
     fp32_pk, fp32_src = fp32_peak_tflops(device, peaks)
+    # expansion: the octant-folded GEMM does 2 K Nb multiply-add flop per volume (K = fundamental voxels),
+    # executed as three BF16 products over the padded shape (K x gemm_N) in the split form; the unfolded
+    # dense contraction it replaces would be 2 V Nb
     mult = 3 if main_form == "bf16split" else 1
-    fl_exp = 2.0 * B * r["V"] * r["Nb"]
+    t_exp = per["expand"] / 1e3
+    fl_exp = 2.0 * B * r["gemm_K"] * r["Nb"]
+    fl_exec = 2.0 * B * r["gemm_K"] * r["gemm_N"] * mult
     pk_exp = peaks.get("bf16_tflops", 1900.0) if mult == 3 else fp32_pk
-    roof_exp = {"kernel": "bh_expand (gather + GEMM + complex)", "bound": "tensor" if mult == 3 else "alu",
-                "achieved": fl_exp / (per["expand"] / 1e3) / 1e12, "unit": "TFLOP/s", "peak": pk_exp,
+    roof_exp = {"kernel": "bh_expand (octant projection + folded GEMM + complex)",
+                "bound": "tensor" if mult == 3 else "alu",
+                "achieved": fl_exp / t_exp / 1e12, "executed": fl_exec / t_exp / 1e12,
+                "dense_equivalent": 2.0 * B * r["V"] * r["Nb"] / t_exp / 1e12, "unit": "TFLOP/s", "peak": pk_exp,
                 "traffic": None,
                 "peak_source": ("MEASURED_PEAKS bf16_tflops (burst), of measured" if mult == 3 else fp32_src)}
-    roof_exp["executed"] = roof_exp["achieved"] * mult
     roof_exp["frac"] = roof_exp["achieved"] / pk_exp
     roof_exp["frac_executed"] = roof_exp["executed"] / pk_exp
-    tuned = (r["tune"]["align_group"], r["tune"]["align_starts_per_thread"])
+    tuned = (r["tune"]["align_group"], r["tune"]["align_starts_per_thread"], r["tune"].get("align_dealing", 1))
     ach = align_flops(w) / (per["align"] / 1e3) / 1e12
-    tr = ALIGN_TRAFFIC_BYTES.get((w.name, tuned[0], tuned[1]))
+    tr = ALIGN_TRAFFIC_BYTES.get((w.name,) + tuned)
     traffic = None
     if tr is not None and tr[2] == align_source_sha():
         traffic = tr[0] * B / tr[1]
-    roof_aln = {"kernel": f"k_align (marching ascent, {tuned[0]} lanes x {tuned[1]} starts per thread)",
+    kname = "k_align_flat" if tuned[2] == 2 else ("k_align_c" if tuned[1] == 2 else "k_align")
+    roof_aln = {"kernel": f"{kname} (marching ascent, {tuned[0]} lanes x {tuned[1]} starts per thread, "
+                          f"{'flat' if tuned[2] == 2 else 'row'} orbit dealing)",
                 "bound": "alu", "achieved": ach, "peak": fp32_pk, "unit": "TFLOP/s", "frac": ach / fp32_pk,
                 "traffic": traffic, "traffic_algorithmic": float(B) * r["Nb"] * 8 + float(B) * w.S * 16,
                 "flop_per_launch": align_flops(w), "ms_per_launch": per["align"],
@@ -463,6 +474,7 @@ def summarize(args, w, res, world, device) -> dict:
                    "l2": "flushed between timed steps (256 MB write); inputs larger than L2",
                    "template": "expanded once before timing (resident)",
                    "autotuned": {"align_lanes_per_group": tuned[0], "align_starts_per_thread": tuned[1],
+                                 "align_orbit_dealing": "flat" if tuned[2] == 2 else "row",
                                  "gemm_n_tile": r["tune"]["gemm_bn"]},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "breakdown_ms_per_step": dict(per, plan_create_s=r["plan_s"]),
@@ -531,14 +543,18 @@ def profile_align(args, device) -> dict:
     score = torch.empty((w.B,), dtype=torch.float32, device=device)
     fl = align_flops(w)
     pk, src = fp32_peak_tflops(device, measured_peaks())
-    variants = [tuple(int(x) for x in v.split("x")) for v in args.variants.split(",")] if args.variants else \
-        [(args.group, args.starts_per_thread)]
+    def parse(v):  # "GxC" (row dealing) or "GxCf" (flat dealing)
+        flat = v.endswith("f")
+        G, C = (int(x) for x in v.rstrip("f").split("x"))
+        return G, C, 2 if flat else 1
+    variants = [parse(v) for v in args.variants.split(",")] if args.variants else \
+        [(args.group, args.starts_per_thread, args.dealing)]
     out = []
-    for G, C in variants:
+    for G, C, D in variants:
         try:
             def run():
                 bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
-                                  group=G, starts_per_thread=C, stream=stream)
+                                  group=G, starts_per_thread=C, dealing=D, stream=stream)
             for _ in range(args.warmup):
                 run()
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -548,12 +564,12 @@ def profile_align(args, device) -> dict:
                 ev[k + 1].record(stream)
             torch.cuda.synchronize(device)
         except bh.BHError as e:
-            out.append({"lanes": G, "starts_per_thread": C, "error": str(e)})
+            out.append({"lanes": G, "starts_per_thread": C, "dealing": D, "error": str(e)})
             continue
         ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         avg = sum(ms) / len(ms)
-        out.append({"lanes": G, "starts_per_thread": C, "ms_per_launch": ms, "achieved_tflops": fl / (avg / 1e3) / 1e12,
-                    "frac": fl / (avg / 1e3) / 1e12 / pk})
+        out.append({"lanes": G, "starts_per_thread": C, "dealing": "flat" if D == 2 else "row", "ms_per_launch": ms,
+                    "achieved_tflops": fl / (avg / 1e3) / 1e12, "frac": fl / (avg / 1e3) / 1e12 / pk})
     plan.destroy()
     return {"profile": "k_align", "workload": describe(w), "flop_per_launch": fl, "peak_tflops": pk,
             "peak_source": src, "align_src_sha": align_source_sha(), "variants": out}
@@ -737,7 +753,7 @@ def wedge_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device) -> dict:
             "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 1}
 
 
-def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509, newton: bool = False) -> dict:
+def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509, newton: bool = False, piece: int = 0) -> dict:
     """Continuous-batching server under a Poisson stream of requests (mean `rate` req/s for `seconds`):
     1-512 subtomograms per request (log-uniform), box edge uniform over {24, 32, 48, 64}, one of 8 resident
     templates (2 per box), 16 starts, bands N/8 -> N/4 -> N/2, 30 steps; noise (SNR 0.1) and a +-60 deg
@@ -750,7 +766,7 @@ def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509, newton: b
     boxes = [24, 32, 48, 64]
     t_setup = time.perf_counter()
     srv = bh.bh_serve_create(hbm_budget_bytes=48 << 30, max_inflight=4, max_batch=2048,
-                             mode=bh.BH_MODE_BF16_SPLIT, steps=8 if newton else 30, newton=newton)
+                             mode=bh.BH_MODE_BF16_SPLIT, steps=8 if newton else 30, newton=newton, piece=piece)
     tids, pools = {}, {}
     for N in boxes:
         tpls = [synth.blob_template(synth.rng_for(40 + N, t), 60, 1.5 * N / 32, 0.75 * N / 2) for t in range(2)]
@@ -794,7 +810,9 @@ def serving_leg(seconds: float, rate: float = 200.0, seed: int = 2509, newton: b
             "setup_s": setup_s,
             "mix": "boxes 24/32/48/64 (l<=N/2, bands N/8-N/4-N/2), 1-512 subtomograms log-uniform, 16 starts, "
                    "8 resident templates, SNR 0.1, +-60 deg wedge, BF16-split expansion",
-            "optimizer": "Newton steps, 8 per band" if newton else "gradient ascent, 30 steps per band"}
+            "optimizer": "Newton steps, 8 per band" if newton else "gradient ascent, 30 steps per band",
+            "piece": piece or 128, "p999_ms": float(np.percentile(lat, 99.9)),
+            "p99_ms_small_requests": float(np.percentile([l for l, (_, B, _, _) in zip(lat, subm) if B <= 32], 99))}
 
 
 def run_mixed(args, device, rank: int = 0, world: int = 1) -> dict:
@@ -869,12 +887,15 @@ def main():
                     help="also measure the 32^3 batch, the mixed batch and the serving loop (N = 1 only)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="serving leg duration, the 60 s window of the serving workload (0 = skip)")
+    ap.add_argument("--serve-piece", type=int, default=0,
+                    help="serving: admit requests in pieces of at most this many subtomograms (0 = the server's 128)")
     ap.add_argument("--serve-newton-seconds", type=float, default=20.0,
                     help="duration of the serving leg with Newton steps (0 = skip)")
     ap.add_argument("--mixed-scale", type=float, default=1.0, help="class-count multiplier of the mixed workload")
     ap.add_argument("--no-autotune", action="store_true", help="use --group/--starts-per-thread instead of tuning")
     ap.add_argument("--group", type=int, default=4, help="lanes per start (group) with --no-autotune")
     ap.add_argument("--starts-per-thread", type=int, default=2, help="starts per thread with --no-autotune")
+    ap.add_argument("--dealing", type=int, default=1, help="orbit dealing with --no-autotune: 1 rows, 2 flat")
     ap.add_argument("--sec3", type=int, default=None,
                     help="also time the Sec. III protocol (candidates + Newton); default on for batch32 / precision64")
     ap.add_argument("--wedge-leg", type=int, default=None,
@@ -967,7 +988,7 @@ def main():
             extra("batch32", batch32)
         extra("mixed", lambda: run_mixed(args, device, rank, world))
         if args.serve_seconds > 0:
-            extra("serving", lambda: serving_leg(args.serve_seconds))
+            extra("serving", lambda: serving_leg(args.serve_seconds, piece=args.serve_piece))
         if args.serve_newton_seconds > 0:
             extra("serving_newton", lambda: serving_leg(args.serve_newton_seconds, newton=True))
     if rank == 0:

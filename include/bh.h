@@ -111,7 +111,7 @@ typedef struct {
  * Build a plan on the current CUDA device: roots and constants in FP64 on the host, the basis
  * table Psi[j][v] (real form, one row per coefficient slot, h^3 folded in) evaluated in FP64
  * and stored on the device in the arithmetic of `mode`, plus the expansion scratch.  With
- * flags = BH_PLAN_MATCH_ONLY the table and scratch are left out (64^3, l <= 32: 13 GB fewer in
+ * flags = BH_PLAN_MATCH_ONLY the table and scratch are left out (64^3, l <= 32: 1.8 GB fewer in
  * BF16-split mode); the expansion calls and the shift search then fail with BH_ERR_ARG.
  * The plan owns all of its device memory and must be used with its device current (other
  * devices: BH_ERR_ARG).  Creation is synchronous.
@@ -129,6 +129,15 @@ int bh_plan_destroy(bh_plan* plan);
 int bh_plan_layout(const bh_plan* plan, int* Nb, int* V, int* offsets);
 /* Options the plan was created with (lambda_max resolved). */
 int bh_plan_info(const bh_plan* plan, bh_plan_opts* opts);
+/*
+ * Shape of the plan's expansion GEMM.  Every real basis row is even or odd under each of the reflections
+ * x -> -x, y -> -y, z -> -z, and the in-ball voxels are symmetric under them, so the expansion runs as 8
+ * block products (one per parity class) over the fundamental voxels x, y, z >= 0 (octant folding, an exact
+ * rewriting of the sum over voxels): *K = fundamental voxels padded to the K block, *N = table rows padded
+ * class by class to the 128-row tile.  The multiply-adds per volume are K * N (against V * Nb unfolded).
+ * Outputs may be NULL.
+ */
+int bh_plan_gemm(const bh_plan* plan, int* K, int* N);
 
 /*
  * Error word of the plan's device waits.  Every wait of the tensor-core expansion pipeline (mbarrier
@@ -160,9 +169,10 @@ int bh_expand(bh_plan* plan, const float* vols, int B, float* coeffs, void* stre
  *   Scratch: a fixed 64 MiB array compiled into the library (a file-scope __device__ array), held on
  *   every GPU where the library's module is loaded until the process exits.  The call allocates
  *   nothing (no cudaMalloc/cudaFree, no allocating library routine).
- *   Limit: one pass needs 128 * (V_pad + Nb_pad) * 4 bytes (V_pad, Nb_pad = voxel and coefficient
- *   counts rounded up to 64 and 256); plans above 64 MiB per pass (for example N = 64, Lmax = 32)
- *   are rejected with BH_ERR_ARG.  Larger B is processed in several passes.
+ *   Limit: one pass needs 128 * (8 K + N) * 4 bytes (K, N from bh_plan_gemm: the 8 parity-class
+ *   projections of each volume over the fundamental voxels and the GEMM output); plans above 64 MiB
+ *   per pass (for example N = 64, Lmax = 32: 88 MB) are rejected with BH_ERR_ARG.  Larger B is
+ *   processed in several passes.
  *   Set-up: the first call on each device looks up the array's device address (cudaGetSymbolAddress)
  *   with that device current; make that first call before any stream capture.
  *   Sharing: all calls use the same array and it keeps the last call's contents (each pass overwrites
@@ -255,6 +265,11 @@ typedef struct {
                              holds C.  Diagnostic, off by default: on voxel data with a missing wedge it
                              reproduces its FP64 reading but lands farther from the ground truth than the
                              plain score (1.8 against 1.0 degrees median on the 32^3 batch) */
+  int dealing;            /* how a group's lanes share the orbits (m, n) of an evaluation: 0 = autotuned
+                             (by rows when not tuned), 1 = row by row (lane q takes n = q - m + kG of row m),
+                             2 = flat across rows (orbit m^2 + m + n to lane (m^2 + m + n) mod G; no lanes
+                             idle at row ends; group 4, 8 or 16, starts_per_thread 1 or 2).  Gradient ascent
+                             only; results differ between dealings by FP32 rounding */
   const int* stage_table;  /* device, B * BH_STAGE_ROW ints or NULL: a marching schedule per subtomogram,
                              row b = (count, band_1 < band_2 < ...), e.g. from bh_choose_bands.  `stages`
                              then gives the largest band any row may use (shared memory, kernel variant)
@@ -401,6 +416,7 @@ typedef struct {
   float align_ms;   /* its time for B subtomograms */
   int gemm_bn;      /* N tile of the tensor-core expansion GEMM (BF16 mode; 0 in FP32 mode) */
   float expand_ms;  /* bh_expand time for B volumes with that tile */
+  int align_dealing; /* orbit dealing of the chosen ascent variant (bh_align_opts.dealing) */
 } bh_tune_result;
 
 /*
@@ -464,6 +480,9 @@ typedef struct {
                               batch, is express; 0 = 2.0 */
   int ingest;              /* 0: read request volumes in place when the device reads pageable host memory
                               coherently, else copy them to the device; 1: always copy */
+  int piece;               /* requests with more subtomograms are admitted in pieces of at most this many,
+                              each next piece queued behind the requests that arrived meanwhile; results
+                              do not depend on it (random starts are drawn per subtomogram); 0 = 128 */
 } bh_serve_opts;
 
 typedef struct {

@@ -47,7 +47,7 @@ def sph_jn(l: int, x):
 def bessel_roots(l: int, lam_max: float) -> np.ndarray:
     """All positive roots lambda_lk of j_l with lambda_lk <= lam_max (+ROOT_SLACK), ascending.
 
-    Sec. II-A: "lambda_lk is the k-th positive root of j_l".  Roots are bracketed
+    Sec. II-A defines lambda_lk as the k-th positive zero of j_l.  Roots are bracketed
     by sign changes on a fine scan (spacing of consecutive roots is about pi) and
     refined by Brent's method.  The first root of j_l exceeds l, so the scan
     starts at l (at 0.5 for l = 0, where j_0 = sin(x)/x)."""

@@ -25,7 +25,7 @@ BH_STAGE_ROW = BH_MAX_STAGES + 1
 
 # every symbol include/bh.h declares (checked by the CPU tests)
 EXPORTS = ["bh_last_error", "bh_status_string", "bh_version", "bh_basis_roots",
-           "bh_plan_create", "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_plan_status",
+           "bh_plan_create", "bh_plan_destroy", "bh_plan_layout", "bh_plan_info", "bh_plan_gemm", "bh_plan_status",
            "bh_plan_probe_wait", "bh_expand", "bh_expand_noalloc", "bh_score_grad", "bh_score_hess",
            "bh_align_batch", "bh_refine_fp64", "bh_align_shifts_workspace", "bh_align_shifts",
            "bh_grid_create", "bh_grid_destroy", "bh_grid_info", "bh_grid_neighbors", "bh_candidates",
@@ -50,7 +50,7 @@ class AlignOpts(ctypes.Structure):
     _fields_ = [("group", ctypes.c_int), ("tmpl_index", ctypes.c_void_p), ("n_templates", ctypes.c_int),
                 ("start_quat_out", ctypes.c_void_p), ("start_score_out", ctypes.c_void_p),
                 ("starts_per_thread", ctypes.c_int), ("refine_fp64", ctypes.c_int), ("newton", ctypes.c_int),
-                ("wedge", ctypes.c_void_p), ("stage_table", ctypes.c_void_p)]
+                ("wedge", ctypes.c_void_p), ("dealing", ctypes.c_int), ("stage_table", ctypes.c_void_p)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
         L.bh_plan_destroy.argtypes = [vp]
         L.bh_plan_layout.argtypes = [vp, vp, vp, vp]
         L.bh_plan_info.argtypes = [vp, ctypes.POINTER(PlanOpts)]
+        L.bh_plan_gemm.argtypes = [vp, vp, vp]
         L.bh_plan_status.argtypes = [vp]
         L.bh_plan_probe_wait.argtypes = [vp, vp]
         L.bh_expand.argtypes = [vp, vp, i, vp, vp]
@@ -153,6 +154,9 @@ class Plan:
         _check(lib().bh_plan_layout(handle, ctypes.addressof(Nb), ctypes.addressof(V), offs.ctypes.data),
                "bh_plan_layout")
         self.Nb, self.V, self.offsets = Nb.value, V.value, offs
+        K, Np = ctypes.c_int(), ctypes.c_int()
+        _check(lib().bh_plan_gemm(handle, ctypes.addressof(K), ctypes.addressof(Np)), "bh_plan_gemm")
+        self.gemm_K, self.gemm_N = K.value, Np.value  # folded expansion GEMM (fundamental voxels, padded rows)
 
     def destroy(self):
         if self.handle:
@@ -239,7 +243,7 @@ def bh_score_hess(plan: Plan, tmpl, sub, quats, L: int, stream=None):
 def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int = 0, tmpl_index=None,
                    n_templates: int = 0, per_start: bool = False, quat_out=None, score_out=None, stream=None,
                    refine_fp64: int = 0, starts_per_thread: int = 0, newton: bool = False, wedge=None,
-                   stage_table=None):
+                   stage_table=None, dealing: int = 0):
     """Multi-start marching ascent.  Returns (quat (B,4), score (B,)) [+ (start_quat (B,S,4), start_score (B,S))]."""
     import torch
     B, S = starts.shape[0], starts.shape[1]
@@ -255,6 +259,7 @@ def bh_align_batch(plan: Plan, tmpl, sub, starts, stages, steps: int, group: int
     o.starts_per_thread = starts_per_thread
     o.refine_fp64 = refine_fp64
     o.newton = int(bool(newton))
+    o.dealing = dealing
     o.wedge = wedge.handle if wedge is not None else None
     if stage_table is not None:
         _need(stage_table, "torch.int32", B * BH_STAGE_ROW, "stage_table")
@@ -477,7 +482,7 @@ def stage_rows(table) -> list[list[int]]:
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("align_group", ctypes.c_int), ("align_starts_per_thread", ctypes.c_int), ("align_ms", ctypes.c_float),
-                ("gemm_bn", ctypes.c_int), ("expand_ms", ctypes.c_float)]
+                ("gemm_bn", ctypes.c_int), ("expand_ms", ctypes.c_float), ("align_dealing", ctypes.c_int)]
 
 
 def bh_autotune(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
@@ -501,7 +506,7 @@ class ServeOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("queue_capacity", ctypes.c_int), ("mode", ctypes.c_int), ("steps", ctypes.c_int),
                 ("newton", ctypes.c_int), ("express_slots", ctypes.c_int), ("express_ms", ctypes.c_double),
-                ("ingest", ctypes.c_int)]
+                ("ingest", ctypes.c_int), ("piece", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -611,10 +616,10 @@ class Server:
 
 def bh_serve_create(hbm_budget_bytes: int = 0, max_inflight: int = 0, max_batch: int = 0, queue_capacity: int = 0,
                     mode: int = BH_MODE_BF16_SPLIT, steps: int = 0, newton: bool = False, express_slots: int = 0,
-                    express_ms: float = 0.0, ingest: int = 0) -> Server:
+                    express_ms: float = 0.0, ingest: int = 0, piece: int = 0) -> Server:
     L = lib()
     o = ServeOpts(hbm_budget_bytes, max_inflight, max_batch, queue_capacity, mode, steps, int(bool(newton)),
-                  express_slots, express_ms, ingest)
+                  express_slots, express_ms, ingest, piece)
     h = ctypes.c_void_p()
     _check(L.bh_serve_create(ctypes.byref(h), ctypes.byref(o)), "bh_serve_create")
     return Server(h.value)

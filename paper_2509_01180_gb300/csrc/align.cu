@@ -50,7 +50,7 @@ constexpr int kBinStride = 2 * kMaxL + 1;
 // Per-band constants of the rescaled recursion, read with a warp-uniform index (every lane of a warp
 // steps through the same l): l >= 2: (1/(l(l-1)), 1/((l-1)^2 (2l-1)(2l-3)), (l-1)^2, l(l+1)); below:
 // (0, 0, 0, l(l+1)).
-__constant__ float4 c_ecoef[kMaxL + 2];
+__constant__ float4 c_ecoef[kMaxL + 4];  // two spare entries: the loops fetch the next pair of bands ahead
 
 constexpr int kMaxStages = 8;
 static_assert(kMaxStages == BH_MAX_STAGES, "schedule rows of the C ABI");
@@ -171,6 +171,12 @@ struct Eval {
   float S, gx, gy, gz;
 };
 
+// g_l = ((l-1)^2 - m^2)((l-1)^2 - n^2) / ((l-1)^2 (2l-1)(2l-3)) of the rescaled recursion for orbit (m, n), from
+// k = c_ecoef[l] (k.z = (l-1)^2, k.y = the inverse denominator), sq2 = m^2 + n^2 and pq2 = m^2 n^2: the
+// numerator a (a - sq2) + pq2 is an integer below 2^24 for l <= 45, exact in FP32, so the one rounding is at the scale
+// (the same value as the two-factor product, in three operations instead of four).
+__device__ __forceinline__ float gcoef(float4 k, float sq2, float pq2) { return fmaf(k.z, k.z - sq2, pq2) * k.y; }
+
 // Score and body-frame gradient (FP32) of C rotations at once (C starts of one subtomogram) at band L, from
 // the orbit table of band Lb >= L.  Every lane of a G-group returns the same (bitwise) results.  For C > 1
 // the evaluation is shared: (C starts of one subtomogram): each orbit-step loads the
@@ -253,6 +259,7 @@ __device__ void eval_rotations(const float4* __restrict__ tab, const float4* __r
         e1[j] = d; e2[j] = 0.f; p1[j] = dp; p2[j] = 0.f;
       }
       const float mn = (float)(m * n), fn2 = (float)(n * n);
+      const float sq2 = fm2 + fn2, pq2 = fm2 * fn2;  // m^2 + n^2, m^2 n^2
       // one step of band l for start j: (E1, E2, P1, P2) -> (EN, PN), accumulated against every table's X
 #define BH_STEP(J, EN, PN, E1, E2, P1, P2, K, G_, X)                                 \
   {                                                                                \
@@ -279,8 +286,8 @@ __device__ void eval_rotations(const float4* __restrict__ tab, const float4* __r
           ep2 += 2 * w;
         }
         ep += 2 * w;
-        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
-        const float g1 = (k1.z - fm2) * (k1.z - fn2) * k1.y;
+        const float g0 = gcoef(k0, sq2, pq2);
+        const float g1 = gcoef(k1, sq2, pq2);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           float ea, pa, eb, pb;
@@ -294,7 +301,7 @@ __device__ void eval_rotations(const float4* __restrict__ tab, const float4* __r
         float4 x0[T];
         x0[0] = ep[w];
         if (T == 2) x0[T - 1] = ep2[w];
-        const float g0 = (k0.z - fm2) * (k0.z - fn2) * k0.y;
+        const float g0 = gcoef(k0, sq2, pq2);
 #pragma unroll
         for (int j = 0; j < C; ++j) {
           float ea, pa;
@@ -353,6 +360,228 @@ __device__ void eval_rotations(const float4* __restrict__ tab, const float4* __r
       out[i].gy = Sb[i] * eg.x - Q * eg.y;
       out[i].gz = Sg[i];
     }
+  }
+}
+
+// Row m of the flat orbit index o = m^2 + m + n (0 <= o < 2^22).
+__device__ __forceinline__ int orbit_row(int o) {
+  int m = (int)sqrtf((float)o);
+  m -= (m * m > o) ? 1 : 0;
+  m += ((m + 1) * (m + 1) <= o) ? 1 : 0;
+  return m;
+}
+
+// z^k, 0 <= k < 2^7, by binary exponentiation (the phases of a lane's first orbit, and the rare jumps of a
+// lane over more than one row).
+__device__ __forceinline__ float2 cpow_bin(float2 z, int k) {
+  float2 r = make_float2(1.f, 0.f);
+  while (k > 0) {
+    if (k & 1) r = cmul(r, z);
+    z = cmul(z, z);
+    k >>= 1;
+  }
+  return r;
+}
+
+// The evaluation of eval_rotations (T = 1) with the orbits dealt in flat order across rows: orbit
+// o = m^2 + m + n, 0 <= o < (L+1)^2, goes to lane o mod G of the group, so consecutive rounds ("chunks") of G
+// orbits straddle row boundaries instead of leaving lanes idle at the end of every row (a row of 2m+1
+// orbits dealt to G lanes idles G - ((2m+1) mod G) lanes for the whole row).  The lanes of a chunk run one
+// l-loop from the chunk's lowest row: a lane whose row starts later has a zero recursion state until its
+// own l = m, where its closed-form seed is injected (a select), so its extra steps add zeros.  Per-orbit
+// phases e^{-i(m alpha + n gamma)} and e^{-i(n alpha + m gamma)} follow the lane from orbit to orbit:
+// within a row they advance by the ratios R1, R2 of an n-step of G, and on a step into the next row
+// (m, n) -> (m+1, n + G - 2m - 2) by the extra factors Ed^2 e^{i gamma (2m+1)} and ed^2 e^{i alpha (2m+1)},
+// themselves advanced by e^{2i gamma}, e^{2i alpha} per row; a jump over several rows (only while 2m+3 < G)
+// recomputes them by binary powers.  The sums over (m, n) are not factored by row, so results differ from
+// eval_rotations by rounding only.
+template <int G, int C>
+__device__ void eval_flat(const float4* __restrict__ tab, int Lb, int L, const float4 (&q)[C], int qg,
+                          const float* __restrict__ lbin, Eval (&out)[C]) {
+  float xb[C], sinb[C], lcc[C], lss[C], rcs[C], rsc[C];
+  float2 es[C], ed[C], R1[C], R2[C], E2g[C], E2a[C], P1[C], P2[C], U1[C], U2[C];
+  const int norb = (L + 1) * (L + 1);
+  int m = orbit_row(qg), n = qg - m * m - m;  // the lane's orbit (m, n); it is live while m <= L
+  int rowbase = tab_base(m, Lb);              // first table entry of row m
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const float w = q[j].x, x = q[j].y, y = q[j].z, z = q[j].w;
+    const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+    es[j] = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+    ed[j] = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+    xb[j] = (cb - sb) * (cb + sb);
+    sinb[j] = 2.f * cb * sb;
+    const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
+    lcc[j] = log2f(cbc);
+    lss[j] = log2f(sbc);
+    rcs[j] = cbc / sbc;
+    rsc[j] = sbc / cbc;
+    const float2 Es = cconj(es[j]), Ed = cconj(ed[j]);
+    const float2 EsG = cpow(Es, G), edG = cpow(ed[j], G);
+    R1[j] = cmul(EsG, edG);
+    R2[j] = cmul(EsG, cconj(edG));
+    const float2 eig = cmul(es[j], Ed), eia = cmul(es[j], ed[j]);  // e^{i gamma}, e^{i alpha}
+    E2g[j] = cmul(eig, eig);
+    E2a[j] = cmul(eia, eia);
+    const float2 pa = cpow_bin(Es, m + n);
+    P1[j] = cmul(pa, cpow_bin(Ed, m - n));
+    P2[j] = cmul(pa, cpow_bin(ed[j], m - n));
+    U1[j] = cmul(cmul(Ed, Ed), cpow_bin(eig, 2 * m + 1));
+    U2[j] = cmul(cmul(ed[j], ed[j]), cpow_bin(eia, 2 * m + 1));
+  }
+  float S[C], Sa[C], Sb[C], Sg[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) S[j] = Sa[j] = Sb[j] = Sg[j] = 0.f;
+  int m_lo = 0, m_hi = 0;  // rows of the chunk's first and last orbits (the same for every lane)
+  for (int c0 = 0; c0 < norb; c0 += G) {
+    while ((m_lo + 1) * (m_lo + 1) <= c0) ++m_lo;
+    const int last = min(c0 + G, norb) - 1;
+    while ((m_hi + 1) * (m_hi + 1) <= last) ++m_hi;
+    const bool live = m <= L;
+    const int wl = live ? 2 * m + 1 : 0;
+    const float4* ep0 = tab + (live ? rowbase + (n + m) : 0);
+    const float lb = live ? __ldg(lbin + m * kBinStride + m + n) : 0.f;
+    const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n, fm = (float)m;
+    const bool odd = (m - n) & 1;
+    const float mn = (float)(m * n), fm2 = (float)(m * m), fn2 = (float)(n * n);
+    const float sq2 = fm2 + fn2, pq2 = fm2 * fn2;  // m^2 + n^2, m^2 n^2
+    float e1[C], e2[C], p1[C], p2[C], ds[C], dps[C];
+    float a1r[C], a1i[C], a2r[C], a2i[C], b1r[C], b1i[C], b2r[C], b2i[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      float d = live ? exp2f(lb + fa * lcc[j] + fd * lss[j]) : 0.f;
+      d = odd ? -d : d;
+      ds[j] = d;
+      dps[j] = 0.5f * d * (fd * rcs[j] - fa * rsc[j]);
+      e1[j] = e2[j] = p1[j] = p2[j] = 0.f;
+      a1r[j] = a1i[j] = a2r[j] = a2i[j] = b1r[j] = b1i[j] = b2r[j] = b2i[j] = 0.f;
+    }
+#define BH_FSTEP(J, EN, PN, E1, E2, P1_, P2_, K, G_, X)                                \
+  {                                                                                 \
+    const float t_ = fmaf(-mn, (K).x, xb[J]);                                       \
+    EN = fmaf(t_, E1, -(G_) * E2);                                                  \
+    PN = fmaf(t_, P1_, -fmaf(sinb[J], E1, (G_) * P2_));                             \
+  }
+#define BH_FACC(J, EN, PN, X)                                                       \
+  {                                                                                 \
+    a1r[J] = fmaf(EN, (X).x, a1r[J]); a1i[J] = fmaf(EN, (X).y, a1i[J]);             \
+    a2r[J] = fmaf(EN, (X).z, a2r[J]); a2i[J] = fmaf(EN, (X).w, a2i[J]);             \
+    b1r[J] = fmaf(PN, (X).x, b1r[J]); b1i[J] = fmaf(PN, (X).y, b1i[J]);             \
+    b2r[J] = fmaf(PN, (X).z, b2r[J]); b2i[J] = fmaf(PN, (X).w, b2i[J]);             \
+  }
+    if (m_lo == m_hi) {  // one row: every live lane starts at l = m_lo with its seed (dead lanes: d = 0)
+      const float4 X = ep0[0];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        e1[j] = ds[j];
+        p1[j] = dps[j];
+        BH_FACC(j, ds[j], dps[j], X);
+      }
+    }
+    // l = m_lo .. m_hi over two or more rows: each lane's orbit starts at its own row m (seed injected
+    // there; zeros before)
+    for (int l = m_lo; l <= m_hi && m_lo < m_hi; ++l) {
+      const float4 X = ep0[(max(l, m) - m) * wl];
+      const float4 k0 = c_ecoef[l];
+      const float g0 = gcoef(k0, sq2, pq2);
+      const bool start = (l == m);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        float en, pn;
+        BH_FSTEP(j, en, pn, e1[j], e2[j], p1[j], p2[j], k0, g0, X);
+        en = start ? ds[j] : en;
+        pn = start ? dps[j] : pn;
+        BH_FACC(j, en, pn, X);
+        e2[j] = e1[j]; e1[j] = en; p2[j] = p1[j]; p1[j] = pn;
+      }
+    }
+    // l = m_hi+1 .. L: every live lane is inside its orbit
+    // four bands per iteration (a loop branch per four steps), then single steps
+    const float4* ep = ep0 + (m_hi + 1 - m) * wl;
+    int l = m_hi + 1;
+    for (; l + 3 <= L; l += 4) {
+      const float4 x0 = ep[0], x1 = ep[wl], x2 = ep[2 * wl], x3 = ep[3 * wl];
+      ep += 4 * wl;
+      const float4 k0 = c_ecoef[l], k1 = c_ecoef[l + 1], k2 = c_ecoef[l + 2], k3 = c_ecoef[l + 3];
+      const float g0 = gcoef(k0, sq2, pq2), g1 = gcoef(k1, sq2, pq2);
+      const float g2 = gcoef(k2, sq2, pq2), g3 = gcoef(k3, sq2, pq2);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        float ea, pa, eb, pb, ec, pc, ee, pe;
+        BH_FSTEP(j, ea, pa, e1[j], e2[j], p1[j], p2[j], k0, g0, x0);
+        BH_FACC(j, ea, pa, x0);
+        BH_FSTEP(j, eb, pb, ea, e1[j], pa, p1[j], k1, g1, x1);
+        BH_FACC(j, eb, pb, x1);
+        BH_FSTEP(j, ec, pc, eb, ea, pb, pa, k2, g2, x2);
+        BH_FACC(j, ec, pc, x2);
+        BH_FSTEP(j, ee, pe, ec, eb, pc, pb, k3, g3, x3);
+        BH_FACC(j, ee, pe, x3);
+        e2[j] = ec; e1[j] = ee; p2[j] = pc; p1[j] = pe;
+      }
+    }
+    for (; l <= L; ++l) {
+      const float4 x0 = ep[0];
+      ep += wl;
+      const float4 k0 = c_ecoef[l];
+      const float g0 = gcoef(k0, sq2, pq2);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        float ea, pa;
+        BH_FSTEP(j, ea, pa, e1[j], e2[j], p1[j], p2[j], k0, g0, x0);
+        BH_FACC(j, ea, pa, x0);
+        e2[j] = e1[j]; e1[j] = ea; p2[j] = p1[j]; p1[j] = pa;
+      }
+    }
+#undef BH_FSTEP
+#undef BH_FACC
+    // the orbit's terms: S += Re z1 + Re z2, dS/dalpha += m Im z1 + n Im z2, dS/dgamma += n Im z1 + m Im z2,
+    // dS/dbeta += Re y1 + Re y2 (z = phase x xi-sum, y = phase x derivative sum)
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const float z1r = P1[j].x * a1r[j] - P1[j].y * a1i[j], z1i = P1[j].x * a1i[j] + P1[j].y * a1r[j];
+      const float z2r = P2[j].x * a2r[j] - P2[j].y * a2i[j], z2i = P2[j].x * a2i[j] + P2[j].y * a2r[j];
+      S[j] += z1r + z2r;
+      Sa[j] = fmaf(fm, z1i, fmaf(fn, z2i, Sa[j]));
+      Sg[j] = fmaf(fn, z1i, fmaf(fm, z2i, Sg[j]));
+      Sb[j] += (P1[j].x * b1r[j] - P1[j].y * b1i[j]) + (P2[j].x * b2r[j] - P2[j].y * b2i[j]);
+    }
+    // the lane's next orbit, G further in flat order: n advances by G (phases by R1, R2); each wrap into
+    // the next row, (m, n) -> (m+1, n - 2m - 2), multiplies them by the row factors U1, U2, which then
+    // advance by e^{2i gamma}, e^{2i alpha}
+    n += G;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      P1[j] = cmul(P1[j], R1[j]);
+      P2[j] = cmul(P2[j], R2[j]);
+    }
+    while (n > m) {
+      n -= 2 * m + 2;
+      rowbase += (2 * m + 1) * (Lb - m + 1);
+      ++m;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        P1[j] = cmul(P1[j], U1[j]);
+        P2[j] = cmul(P2[j], U2[j]);
+        U1[j] = cmul(U1[j], E2g[j]);
+        U2[j] = cmul(U2[j], E2a[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const float2 eg = cmul(es[j], cconj(ed[j]));
+#pragma unroll
+    for (int s = 1; s < G; s <<= 1) {
+      S[j] += __shfl_xor_sync(0xffffffffu, S[j], s);
+      Sa[j] += __shfl_xor_sync(0xffffffffu, Sa[j], s);
+      Sb[j] += __shfl_xor_sync(0xffffffffu, Sb[j], s);
+      Sg[j] += __shfl_xor_sync(0xffffffffu, Sg[j], s);
+    }
+    const float Q = (sinb[j] > 1e-30f) ? (xb[j] * Sg[j] - Sa[j]) / sinb[j] : 0.f;
+    out[j].S = S[j];
+    out[j].gx = Sb[j] * eg.y + Q * eg.x;
+    out[j].gy = Sb[j] * eg.x - Q * eg.y;
+    out[j].gz = Sg[j];
   }
 }
 
@@ -569,6 +798,12 @@ __device__ void load_schedule(const AlignArgs& a, int p, int* sched) {
 // or two warps) keep 8 resident CTAs (shared memory holds 7 orbit tables of band 16); larger blocks are
 // used when the table is large and few CTAs fit, so they get at least 128 registers per thread.
 __host__ __device__ constexpr int min_blocks(int NT) { return NT <= 64 ? 8 : NT <= 128 ? 4 : NT <= 256 ? 2 : 1; }
+// Kernels that carry C starts per thread need about 180 registers at C = 2: a CTA of NT threads is given
+// up to 255 (at least 8 warps' worth of register file per SM), so that the launch bound does not force
+// spills; residency then follows from registers and the orbit tables' shared memory.
+__host__ __device__ constexpr int min_blocks_c(int NT, int C) {
+  return C == 1 ? min_blocks(NT) : (NT <= 32 ? 8 : NT <= 64 ? 4 : NT <= 128 ? 2 : 1);
+}
 
 // Multi-start marching ascent; one CTA per subtomogram, blockDim = NT = roundup(S*G, 32).
 template <int G, int NT>
@@ -882,7 +1117,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_wedge(const AlignA
 
 // Marching ascent with C starts per thread: CTA of NT = roundup(S/C * G, 32) threads per subtomogram.
 template <int G, int C, int NT>
-__global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs a) {
+__global__ void __launch_bounds__(NT, min_blocks_c(NT, C)) k_align_c(const AlignArgs a) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
   __shared__ int sched[kMaxStages + 1];
@@ -924,6 +1159,88 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_align_c(const AlignArgs 
       }
       Eval tr[C];
       eval_rotations<G, C>(smem_tab, nullptr, Lb, L, qt, qg, a.lbin, tr);
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        if (!stop[j]) {
+          if (tr[j].S > cur[j].S) {
+            q[j] = qt[j];
+            cur[j] = tr[j];
+            h[j] = fminf(1.5f * h[j], hmax);
+          } else {
+            h[j] *= 0.5f;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  float* sS = reinterpret_cast<float*>(smem_tab);
+  float4* sQ = reinterpret_cast<float4*>(sS + ((a.S + 3) & ~3));
+  if (active && qg == 0) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int s = chunk * C + j;
+      sS[s] = cur[j].S;
+      sQ[s] = q[j];
+      if (a.start_quat_out) a.start_quat_out[(size_t)p * a.S + s] = q[j];
+      if (a.start_score_out) a.start_score_out[(size_t)p * a.S + s] = cur[j].S;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int j = 1; j < a.S; ++j)
+      if (sS[j] > sS[best]) best = j;
+    a.quat_out[p] = sQ[best];
+    a.score_out[p] = sS[best];
+  }
+}
+
+// Marching ascent with the orbits dealt in flat order (eval_flat), C starts per thread; CTA of
+// NT = roundup(S/C * G, 32) threads per subtomogram.
+template <int G, int C, int NT>
+__global__ void __launch_bounds__(NT, min_blocks_c(NT, C)) k_align_flat(const AlignArgs a) {
+  extern __shared__ float4 smem_tab[];
+  const int p = blockIdx.x;
+  __shared__ int sched[kMaxStages + 1];
+  load_schedule(a, p, sched);
+  const int Lb = sched[sched[0]];
+  const int chunk = threadIdx.x / G, qg = threadIdx.x % G;
+  const int nchunks = a.S / C;
+  const bool active = chunk < nchunks;
+  const int ce = active ? chunk : chunk % nchunks;
+  build_table(smem_tab, a.lay, template_row(a, p), a.sub + (size_t)p * a.lay.Nb, a.P, Lb, threadIdx.x,
+              blockDim.x);
+  __syncthreads();
+  float4 q[C];
+  Eval cur[C];
+  float h[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    q[j] = qnormalize(a.starts[(size_t)p * a.S + ce * C + j]);
+    cur[j].S = cur[j].gx = cur[j].gy = cur[j].gz = 0.f;
+  }
+  for (int st = 0; st < sched[0]; ++st) {
+    const int L = sched[1 + st];
+    const float hmax = 3.14159265358979f / (float)L;
+#pragma unroll
+    for (int j = 0; j < C; ++j) h[j] = 0.5f * hmax;
+    eval_flat<G, C>(smem_tab, Lb, L, q, qg, a.lbin, cur);
+    for (int t = 0; t < a.steps; ++t) {
+      float4 qt[C];
+      bool stop[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float gn = sqrtf(cur[j].gx * cur[j].gx + cur[j].gy * cur[j].gy + cur[j].gz * cur[j].gz);
+        stop[j] = !(gn > 1e-12f * fabsf(cur[j].S));
+        const float inv = stop[j] ? 0.f : 1.f / gn;
+        float sh, ch;
+        sincosf(stop[j] ? 0.f : 0.5f * h[j], &sh, &ch);
+        const float4 dq = make_float4(ch, sh * cur[j].gx * inv, sh * cur[j].gy * inv, sh * cur[j].gz * inv);
+        qt[j] = qnormalize(qmul(q[j], dq));
+      }
+      Eval tr[C];
+      eval_flat<G, C>(smem_tab, Lb, L, qt, qg, a.lbin, tr);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         if (!stop[j]) {
@@ -1311,6 +1628,56 @@ int launch_align_c2_g(const AlignArgs& a, cudaStream_t stream) {
   }
 }
 
+template <int G, int C, int NT>
+int launch_align_flat_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
+  static SmemAttr have;
+  int st = ensure_smem(k_align_flat<G, C, NT>, have, smem);
+  if (st != BH_OK) return st;
+  k_align_flat<G, C, NT><<<a.B, NT, smem, stream>>>(a);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+template <int G, int C>
+int launch_align_flat_gc(const AlignArgs& a, cudaStream_t stream) {
+  const int threads = round_up((a.S / C) * G, 32);
+  const size_t sel = (size_t)((a.S + 3) & ~3) * sizeof(float) + (size_t)a.S * sizeof(float4);
+  const size_t smem = std::max(table_bytes(a.Lb), sel);
+  if (smem > 232448) return fail(BH_ERR_UNSUPPORTED, "orbit table for band %d needs %zu B of shared memory", a.Lb, smem);
+  switch (threads) {
+    case 32: return launch_align_flat_nt<G, C, 32>(a, smem, stream);
+    case 64: return launch_align_flat_nt<G, C, 64>(a, smem, stream);
+    case 96:
+    case 128: return launch_align_flat_nt<G, C, 128>(a, smem, stream);
+    case 160:
+    case 192:
+    case 224:
+    case 256: return launch_align_flat_nt<G, C, 256>(a, smem, stream);
+    default: return launch_align_flat_nt<G, C, 512>(a, smem, stream);
+  }
+}
+
+// Flat orbit dealing (eval_flat): G lanes per group of C starts (S a multiple of C).
+int launch_align_flat(const AlignArgs& a, int G, int C, cudaStream_t stream) {
+  if (a.S % C) return fail(BH_ERR_ARG, "%d starts per thread need S divisible by it (S=%d)", C, a.S);
+  if (C == 1) {
+    switch (G) {
+      case 4: return launch_align_flat_gc<4, 1>(a, stream);
+      case 8: return launch_align_flat_gc<8, 1>(a, stream);
+      case 16: return launch_align_flat_gc<16, 1>(a, stream);
+      default: break;
+    }
+  } else if (C == 2) {
+    switch (G) {
+      case 4: return launch_align_flat_gc<4, 2>(a, stream);
+      case 8: return launch_align_flat_gc<8, 2>(a, stream);
+      case 16: return launch_align_flat_gc<16, 2>(a, stream);
+      default: break;
+    }
+  }
+  return fail(BH_ERR_ARG, "flat dealing: group %d with %d starts per thread not in {4,8,16} x {1,2}", G, C);
+}
+
 // Two starts per thread (S even): G lanes per pair of starts.
 int launch_align_c2(const AlignArgs& a, int G, cudaStream_t stream) {
   if (a.S % 2) return fail(BH_ERR_ARG, "two starts per thread need an even S (S=%d)", a.S);
@@ -1485,8 +1852,8 @@ int align_init_constants() {
   BH_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
   if (dev >= 0 && dev < 128 && done[dev]) return BH_OK;
-  float4 ec[kMaxL + 2];
-  for (int l = 0; l < kMaxL + 2; ++l) {
+  float4 ec[kMaxL + 4];
+  for (int l = 0; l < kMaxL + 4; ++l) {
     if (l < 2) {
       ec[l] = make_float4(0.f, 0.f, 0.f, (float)(l * (l + 1)));
     } else {
@@ -1617,7 +1984,7 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   a.lbin = p->d_lbin;
   a.quat_out = reinterpret_cast<float4*>(quat_out);
   a.score_out = score_out;
-  int G = 0, C = 0;
+  int G = 0, C = 0, D = 0;
   if (opts) {
     if (opts->tmpl_index) {
       if (opts->n_templates < 1) return fail(BH_ERR_ARG, "n_templates=%d with tmpl_index", opts->n_templates);
@@ -1629,7 +1996,9 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     a.stage_table = opts->stage_table;
     G = opts->group;
     C = opts->starts_per_thread;
+    D = opts->dealing;
     if (C < 0 || C > 2) return fail(BH_ERR_ARG, "starts_per_thread=%d not in {0,1,2}", C);
+    if (D < 0 || D > 2) return fail(BH_ERR_ARG, "dealing=%d not in {0,1,2}", D);
     if (opts->refine_fp64 < 0 || opts->refine_fp64 > kMaxRefine)
       return fail(BH_ERR_ARG, "refine_fp64=%d outside 0..%d", opts->refine_fp64, kMaxRefine);
     if (opts->refine_fp64 > 0 && (!opts->start_quat_out || !opts->start_score_out))
@@ -1638,13 +2007,15 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
   if (G == 0) {
     auto it = p->align_group.find({a.Lb, S});
     if (it != p->align_group.end()) {
-      G = it->second.first;
-      if (C == 0) C = it->second.second;
+      G = it->second.group;
+      if (C == 0) C = it->second.starts_per_thread;
+      if (D == 0) D = it->second.dealing;
     } else {
       G = default_group(S, a.Lb);
     }
   }
   if (C == 0) C = 1;
+  if (D == 0) D = 1;
   if (opts && opts->wedge) {
     const bh_wedge* w = opts->wedge;
     if (opts->newton || opts->starts_per_thread > 1)
@@ -1665,6 +2036,10 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     if (round_up(S * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
     st = launch_newton(a, G, false, 0, static_cast<cudaStream_t>(stream));
+  } else if (D == 2) {
+    if (round_up((S / C) * G, 32) > kMaxThreads)
+      return fail(BH_ERR_ARG, "S/%d*group = %d exceeds %d threads", C, (S / C) * G, kMaxThreads);
+    st = launch_align_flat(a, G, C, static_cast<cudaStream_t>(stream));
   } else if (C == 2) {
     if (round_up((S / 2) * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S/2*group = %d exceeds %d threads", (S / 2) * G, kMaxThreads);
@@ -1753,16 +2128,19 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
   AT_TRY(cudaMemsetAsync(coef, 0x3C, (size_t)B * p->Nb * 8, st));
   AT_TRY(cudaMemsetAsync(tmpl, 0x3C, (size_t)p->Nb * 8, st));
   AT_TRY(cudaMemsetAsync(starts, 0x3C, (size_t)B * S * 16, st));
-  int best_g = 0, best_c = 1;
+  int best_g = 0, best_c = 1, best_d = 1;
   float best_ms = 1e30f;
-  const int cand[][2] = {{1, 1}, {2, 1}, {4, 1}, {8, 1}, {16, 1}, {2, 2}, {4, 2}, {8, 2}, {16, 2}};
+  // (lanes, starts per thread, dealing: 1 by rows, 2 flat)
+  const int cand[][3] = {{1, 1, 1}, {2, 1, 1}, {4, 1, 1}, {8, 1, 1}, {16, 1, 1}, {2, 2, 1}, {4, 2, 1}, {8, 2, 1},
+                         {16, 2, 1}, {4, 1, 2}, {8, 1, 2}, {16, 1, 2}, {4, 2, 2}, {8, 2, 2}, {16, 2, 2}};
   for (const auto& gc : cand) {
-    const int G = gc[0], C = gc[1];
+    const int G = gc[0], C = gc[1], Dv = gc[2];
     if (C == 2 && (S % 2)) continue;
     if (round_up((S / C) * G, 32) > kMaxThreads) continue;
     bh_align_opts o{};
     o.group = G;
     o.starts_per_thread = C;
+    o.dealing = Dv;
     int rc = BH_OK;
     for (int it = 0; it < 2 && rc == BH_OK; ++it)
       rc = bh_align_batch(p, tmpl, coef, B, starts, S, stages, nstages, steps, quat, score, &o, st);
@@ -1778,13 +2156,14 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
       best_ms = ms;
       best_g = G;
       best_c = C;
+      best_d = Dv;
     }
   }
   if (best_g == 0) {
     cleanup();
     return fail(BH_ERR_UNSUPPORTED, "no alignment variant runs for S=%d band %d", S, Lb);
   }
-  p->align_group[{Lb, S}] = {best_g, best_c};
+  p->align_group[{Lb, S}] = {best_g, best_c, best_d};
   int best_bn = 0;
   float best_ems = 0.f;
   if (p->mode == BH_MODE_BF16_SPLIT && !p->match_only) {
@@ -1818,6 +2197,7 @@ extern "C" int bh_autotune(bh_plan* p, int B, int S, const int* stages, int nsta
   if (out) {
     out->align_group = best_g;
     out->align_starts_per_thread = best_c;
+    out->align_dealing = best_d;
     out->align_ms = best_ms;
     out->gemm_bn = best_bn;
     out->expand_ms = best_ems;

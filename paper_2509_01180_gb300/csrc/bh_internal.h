@@ -90,11 +90,24 @@ struct Layout {
   int K[kMaxL + 1];
 };
 
-// GEMM tiling of the tensor-core expansion.
+// GEMM tiling of the expansion (tensor-core and FP32 forms).
 constexpr int kGemmBM = 128;
+constexpr int kGemmBN = 128;  // every parity class of table rows is padded to a multiple of the N tile
 constexpr int kGemmBK = 64;
-constexpr int kPadV = 64;    // V is padded to a multiple of the K block
-constexpr int kPadNb = 256;  // Nb is padded to a multiple of 256 (FP32 and tensor-core N tiles divide it)
+constexpr int kPadV = 64;     // the fundamental voxels are padded to a multiple of the K block
+
+// Octant folding of the expansion GEMM: table rows come class by class (8 parity classes), N tiles
+// [ntile_end[c-1], ntile_end[c]) belong to class c, and class c's projected volumes are the rows
+// [c rows, (c+1) rows) of the X operand.  rows = 0 turns the mapping off (one plain GEMM).
+struct ClassMap {
+  int ntile_end[8];
+  int rows;
+};
+__host__ __device__ inline int class_of_ntile(const ClassMap& cm, int nt) {
+  int c = 0;
+  while (c < 7 && nt >= cm.ntile_end[c]) ++c;
+  return c;
+}
 
 }  // namespace bh
 
@@ -103,19 +116,21 @@ struct bh_plan {
   int N = 0, Lmax = 0, mode = 0, max_batch = 0;
   bool match_only = false;          // BH_PLAN_MATCH_ONLY: no expansion table or scratch
   double lam_max = 0;
-  int V = 0, V_pad = 0, Nb = 0, Nb_pad = 0, M_cap = 0;
+  int V = 0, Nb = 0, Nb_pad = 0, M_cap = 0;  // in-ball voxels, coefficients, padded table rows, rows/pass
+  int VF = 0, VF_pad = 0;                     // fundamental voxels (x, y, z >= 0) = the GEMM's K
+  bh::ClassMap cls{};                         // N tiles of each parity class (rows set per launch)
   std::vector<int> K, offs;         // per degree
   std::vector<double> lam, cst;     // lambda_lk, c_lk flattened by degree
   bh::Layout layout{};
 
-  int* d_vox = nullptr;             // [V] flat voxel index of each in-ball voxel
+  int* d_fund = nullptr;            // [VF] fundamental voxel coordinates x | y << 10 | z << 20
   int2* d_slot = nullptr;           // [Nb] real-GEMM columns feeding each complex slot (signed, 1-based)
-  float* d_T32 = nullptr;           // [Nb_pad][V_pad] basis table, FP32 mode
-  __nv_bfloat16* d_Thi = nullptr;   // [Nb_pad][V_pad] BF16 hi part
-  __nv_bfloat16* d_Tlo = nullptr;   // [Nb_pad][V_pad] BF16 lo part
-  float* d_X32 = nullptr;           // [M_cap][V_pad] gathered volumes (FP32 mode)
-  __nv_bfloat16* d_Xhi = nullptr;   // [M_cap][V_pad] gathered volumes, hi part
-  __nv_bfloat16* d_Xlo = nullptr;   // [M_cap][V_pad] lo part
+  float* d_T32 = nullptr;           // [Nb_pad][VF_pad] basis table by parity class, FP32 mode
+  __nv_bfloat16* d_Thi = nullptr;   // [Nb_pad][VF_pad] BF16 hi part
+  __nv_bfloat16* d_Tlo = nullptr;   // [Nb_pad][VF_pad] BF16 lo part
+  float* d_X32 = nullptr;           // [8][M_cap][VF_pad] projected volumes per class (FP32 mode)
+  __nv_bfloat16* d_Xhi = nullptr;   // [8][M_cap][VF_pad] projected volumes, hi part
+  __nv_bfloat16* d_Xlo = nullptr;   // [8][M_cap][VF_pad] lo part
   float* d_C = nullptr;             // [ksplit_max][M_cap][Nb_pad] real GEMM output (per K split)
   int* d_err = nullptr;             // device status word written by bounded waits
   float* d_P = nullptr;             // orbit-table scale P_l(m,n), layout [m][l][n] for l <= Lmax
@@ -126,7 +141,10 @@ struct bh_plan {
   int num_sms = 152;                // SMs of the device (split-K sizing)
   int ksplit_max = 1;               // K splits the GEMM-output scratch holds
   CUtensorMap tm_xhi, tm_xlo, tm_thi, tm_tlo;  // TMA descriptors (BF16 mode)
-  std::map<std::pair<int, int>, std::pair<int, int>> align_group;  // autotuned (lanes, starts per thread) by (band, S)
+  struct AlignVariant {
+    int group, starts_per_thread, dealing;
+  };
+  std::map<std::pair<int, int>, AlignVariant> align_group;  // autotuned ascent variant by (band, S)
   std::map<std::pair<int, int>, int> newton_group;                 // autotuned lanes per start of the Newton kernel
 };
 

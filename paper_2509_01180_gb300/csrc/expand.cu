@@ -9,6 +9,9 @@
 //                       TMEM.  X = Xh + Xl and T = Th + Tl are split into BF16 hi/lo parts and the three
 //                       products Xh*Th + Xh*Tl + Xl*Th accumulate into the same tile (the Xl*Tl term,
 //                       ~2^-16 relative, is dropped).
+// The GEMM runs over the fundamental voxels only (octant folding, see plan.cpp): each volume is first
+// projected onto the 8 parity classes (k_project), and the table rows of class c are contracted with the
+// class-c projection, so one launch computes 8 block products of one eighth of the voxels each.
 // The real GEMM columns are then combined into complex coefficients [b][l][k][m+l].
 #include <cstdio>
 
@@ -18,18 +21,18 @@ namespace bh {
 namespace {
 
 // ---------------------------------------------------------------- basis table (FP64 -> storage form)
+// Row j (a table column of the GEMM, class by class) at fundamental voxel v; padding rows (colinfo -1) and
+// padding voxels are zero.
 __global__ void k_build_table(const double* __restrict__ radial, int n_r2, const double* __restrict__ angular,
                               const int* __restrict__ vox_r2, const int2* __restrict__ colinfo, double h3, int V,
-                              int V_pad, int Nb, float* __restrict__ T32, __nv_bfloat16* __restrict__ Thi,
+                              int V_pad, float* __restrict__ T32, __nv_bfloat16* __restrict__ Thi,
                               __nv_bfloat16* __restrict__ Tlo) {
   const int j = blockIdx.y;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V_pad) return;
   double val = 0.0;
-  if (j < Nb && v < V) {
-    const int2 ci = colinfo[j];
-    val = h3 * radial[(size_t)ci.x * n_r2 + vox_r2[v]] * angular[(size_t)ci.y * V + v];
-  }
+  const int2 ci = colinfo[j];
+  if (ci.x >= 0 && v < V) val = h3 * radial[(size_t)ci.x * n_r2 + vox_r2[v]] * angular[(size_t)ci.y * V + v];
   const size_t o = (size_t)j * V_pad + v;
   if (T32) T32[o] = (float)val;
   if (Thi) {
@@ -39,79 +42,95 @@ __global__ void k_build_table(const double* __restrict__ radial, int n_r2, const
   }
 }
 
-// ---------------------------------------------------------------- gather in-ball voxels (+ hi/lo split)
-// Row b of X = the in-ball voxels of volume b (zero beyond V and for padding rows), as FP32 or as a BF16
-// hi/lo split (x = hi + lo to ~2^-16).  Four consecutive voxels per thread (V_pad is a multiple of 64):
-// one 16-byte index load, four independent gathers, one 16-byte (FP32) or two 8-byte (BF16) stores.
+// ---------------------------------------------------------------- octant projection (+ hi/lo split)
+// Row b of class c (X rows c * cls_rows + b) at fundamental voxel u = (x, y, z >= 0):
+//   G_c(u) = 2^{-zeros(u)} sum_{s in {0..7}} (-1)^{popcount(c & s)} f(image_s(u)),
+// image_s flipping the sign of axis i when bit i of s is set; a fast Walsh-Hadamard transform over the 8
+// images (three butterfly stages), then the scale (coincident images on a zero coordinate counted once).
 // kPtr: volume b starts at vptr[b] (a table of B addresses, e.g. request buffers in host memory that the
-// device reads coherently) instead of vols + b N^3.
-template <bool kPtr>
-__global__ void k_gather4(const float* __restrict__ vols, const float* const* __restrict__ vptr, int B, long long N3,
-                          const int* __restrict__ vox, int V, int V_pad, float* __restrict__ X32,
-                          __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo) {
-  const int b = blockIdx.y;
-  const int v = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (v >= V_pad) return;
-  float x[4] = {0.f, 0.f, 0.f, 0.f};
-  if (b < B) {
-    const float* vb = kPtr ? vptr[b] : vols + (size_t)b * N3;
-    if (v + 4 <= V) {
-      const int4 id = __ldg(reinterpret_cast<const int4*>(vox + v));
-      x[0] = __ldg(vb + id.x);
-      x[1] = __ldg(vb + id.y);
-      x[2] = __ldg(vb + id.z);
-      x[3] = __ldg(vb + id.w);
-    } else {
+// device reads coherently).  shift (optional): f is read at image + shift, zero outside the box (the shift
+// search's f_s(x) = f(x + s)); rows then index (volume, shift) pairs, r = b * nshift + j.
+__device__ __forceinline__ void store_classes(float (&g)[8], size_t o, size_t cls_stride, float* __restrict__ X32,
+                                              __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (v + u < V) x[u] = __ldg(vb + vox[v + u]);
+  for (int c = 0; c < 8; ++c) {
+    const size_t oc = o + (size_t)c * cls_stride;
+    if (X32) X32[oc] = g[c];
+    if (Xhi) {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(g[c]);
+      Xhi[oc] = hi;
+      Xlo[oc] = __float2bfloat16_rn(g[c] - __bfloat162float(hi));
     }
-  }
-  const size_t o = (size_t)b * V_pad + v;
-  if (X32) *reinterpret_cast<float4*>(X32 + o) = make_float4(x[0], x[1], x[2], x[3]);
-  if (Xhi) {
-    __nv_bfloat16 hi[4], lo[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      hi[u] = __float2bfloat16_rn(x[u]);
-      lo[u] = __float2bfloat16_rn(x[u] - __bfloat162float(hi[u]));
-    }
-    uint2 ph, pl;
-    ph.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
-    ph.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
-    pl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
-    pl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
-    *reinterpret_cast<uint2*>(Xhi + o) = ph;
-    *reinterpret_cast<uint2*>(Xlo + o) = pl;
   }
 }
 
-// ---------------------------------------------------------------- gather of shifted volumes
-// Row r = b * nshift + j holds the in-ball voxels of f_s(x) = f(x + s_j) for volume b (zero where x + s_j
-// leaves the box); shifts are integer voxels (sx, sy, sz).
-__global__ void k_gather_shifted(const float* __restrict__ vols, int B, int N, const int* __restrict__ vox,
-                                 const int3* __restrict__ shifts, int nshift, int row0, int rows, int V, int V_pad,
-                                 float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
-                                 __nv_bfloat16* __restrict__ Xlo) {
-  const int rr = blockIdx.y;  // row within this pass
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V_pad) return;
+__device__ __forceinline__ void walsh8(float (&g)[8], int zeros) {
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+      if (!(s & bit)) {
+        const float a = g[s], b = g[s | bit];
+        g[s] = a + b;
+        g[s | bit] = a - b;
+      }
+  const float sc = zeros == 0 ? 1.f : zeros == 1 ? 0.5f : zeros == 2 ? 0.25f : 0.125f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) g[c] *= sc;
+}
+
+template <bool kPtr>
+__global__ void k_project(const float* __restrict__ vols, const float* const* __restrict__ vptr, int B, int N,
+                          const int* __restrict__ fund, int VF, int VF_pad, size_t cls_stride,
+                          float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi, __nv_bfloat16* __restrict__ Xlo) {
+  const int b = blockIdx.y;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= VF_pad) return;
+  float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int zeros = 0;
+  if (b < B && u < VF) {
+    const float* vb = kPtr ? vptr[b] : vols + (size_t)b * N * N * N;
+    const int pk = __ldg(fund + u), h = N / 2;
+    const int x = pk & 1023, y = (pk >> 10) & 1023, z = pk >> 20;
+    zeros = (x == 0) + (y == 0) + (z == 0);
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int ix = h + ((s & 1) ? -x : x), iy = h + ((s & 2) ? -y : y), iz = h + ((s & 4) ? -z : z);
+      g[s] = __ldg(vb + ((size_t)iz * N + iy) * N + ix);
+    }
+    walsh8(g, zeros);
+  }
+  store_classes(g, (size_t)b * VF_pad + u, cls_stride, X32, Xhi, Xlo);
+}
+
+// Projection of shifted volumes: row rr of this pass is pair r = row0 + rr = (volume r / nshift, shift r % nshift).
+__global__ void k_project_shifted(const float* __restrict__ vols, int B, int N, const int* __restrict__ fund,
+                                  const int3* __restrict__ shifts, int nshift, int row0, int rows, int VF, int VF_pad,
+                                  size_t cls_stride, float* __restrict__ X32, __nv_bfloat16* __restrict__ Xhi,
+                                  __nv_bfloat16* __restrict__ Xlo) {
+  const int rr = blockIdx.y;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= VF_pad) return;
+  float g[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int r = row0 + rr;
-  float x = 0.0f;
-  if (rr < rows && v < V) {
-    const int b = r / nshift, j = r % nshift;
-    const int idx = vox[v];
-    const int ix = idx % N + shifts[j].x, iy = (idx / N) % N + shifts[j].y, iz = idx / (N * N) + shifts[j].z;
-    if (b < B && ix >= 0 && ix < N && iy >= 0 && iy < N && iz >= 0 && iz < N)
-      x = __ldg(vols + (size_t)b * N * N * N + ((size_t)iz * N + iy) * N + ix);
+  if (rr < rows && u < VF) {
+    const int bvol = r / nshift, j = r % nshift;
+    if (bvol < B) {
+      const float* vb = vols + (size_t)bvol * N * N * N;
+      const int pk = __ldg(fund + u), h = N / 2;
+      const int x = pk & 1023, y = (pk >> 10) & 1023, z = pk >> 20;
+      const int3 sh = shifts[j];
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int ix = h + ((s & 1) ? -x : x) + sh.x, iy = h + ((s & 2) ? -y : y) + sh.y,
+                  iz = h + ((s & 4) ? -z : z) + sh.z;
+        const bool in = ix >= 0 && ix < N && iy >= 0 && iy < N && iz >= 0 && iz < N;
+        g[s] = in ? __ldg(vb + ((size_t)iz * N + iy) * N + ix) : 0.f;
+      }
+      walsh8(g, (x == 0) + (y == 0) + (z == 0));
+    }
   }
-  const size_t o = (size_t)rr * V_pad + v;
-  if (X32) X32[o] = x;
-  if (Xhi) {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-    Xhi[o] = hi;
-    Xlo[o] = __float2bfloat16_rn(x - __bfloat162float(hi));
-  }
+  store_classes(g, (size_t)rr * VF_pad + u, cls_stride, X32, Xhi, Xlo);
 }
 
 // ---------------------------------------------------------------- real columns -> complex coefficients
@@ -161,7 +180,7 @@ constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 16, SG_PAD = 4;
 
 __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, const float* __restrict__ Bm,
                                                   float* __restrict__ C, int M, int N, int K, int k_split,
-                                                  size_t split_stride) {
+                                                  size_t split_stride, ClassMap cm) {
   // split z of the grid covers K range [z k_split, min(K, (z+1) k_split)) and writes C + z split_stride
   const int kbeg = blockIdx.z * k_split;
   const int kend = min(K, kbeg + k_split);
@@ -172,7 +191,9 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, c
   const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;  // M fastest: CTAs in flight share table panels
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: rows lr and lr+64, k columns lk..lk+3
   const int tx = tid & 15, ty = tid >> 4;
-  const float* Ap0 = A + (size_t)(m0 + lr) * K + kbeg + lk;
+  // octant folding: the A rows of this N tile's parity class (cm.rows = 0: a plain GEMM)
+  const int arow0 = (cm.rows ? class_of_ntile(cm, blockIdx.y) * cm.rows : 0) + m0;
+  const float* Ap0 = A + (size_t)(arow0 + lr) * K + kbeg + lk;
   const float* Ap1 = Ap0 + (size_t)64 * K;
   const float* Bp0 = Bm + (size_t)(n0 + lr) * K + kbeg + lk;
   const float* Bp1 = Bp0 + (size_t)64 * K;
@@ -226,7 +247,7 @@ __global__ void __launch_bounds__(256) k_sgemm_nt(const float* __restrict__ A, c
 int sgemm_nt(const float* A, const float* Bm, float* C, int M, int N, int K, cudaStream_t stream) {
   if (M % SG_BM || N % SG_BN || K % SG_BK || M <= 0 || N <= 0 || K <= 0)
     return fail(BH_ERR_ARG, "sgemm_nt: M=%d N=%d K=%d not tile multiples", M, N, K);
-  k_sgemm_nt<<<dim3(M / SG_BM, N / SG_BN, 1), 256, 0, stream>>>(A, Bm, C, M, N, K, K, 0);
+  k_sgemm_nt<<<dim3(M / SG_BM, N / SG_BN, 1), 256, 0, stream>>>(A, Bm, C, M, N, K, K, 0, ClassMap{});
   BH_CHECK_LAUNCH();
   return BH_OK;
 }
@@ -386,7 +407,7 @@ __global__ void __launch_bounds__(192, 1)
     k_gemm_tc_promoted(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                        const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                        float* __restrict__ C, int ldc, int num_kb_total, int kb_split, size_t split_stride,
-                       int* __restrict__ err) {
+                       int* __restrict__ err, ClassMap cm) {
   // split z of the grid covers K blocks [z kb_split, min(total, (z+1) kb_split)) and writes C + z split_stride
   const int kb_first = blockIdx.z * kb_split;
   const int num_kb = min(num_kb_total - kb_first, kb_split);
@@ -400,6 +421,8 @@ __global__ void __launch_bounds__(192, 1)
   // M tiles vary fastest across the grid, so the CTAs in flight share table (B) panels, the operand
   // larger than L2, while the gathered volumes (A) stay L2-resident
   const int m0 = blockIdx.x * PCfg::BM, n0 = blockIdx.y * PBN;
+  // octant folding: this N tile's parity class reads the projected volumes of that class (A rows)
+  const int arow0 = (cm.rows ? class_of_ntile(cm, blockIdx.y) * cm.rows : 0) + m0;
   const int nchunks = (num_kb + KCHUNK - 1) / KCHUNK;
   auto sA_hi = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES; };
   auto sA_lo = [&](int s) { return smem + (size_t)s * PCfg::STAGE_BYTES + PCfg::A_BYTES; };
@@ -436,8 +459,8 @@ __global__ void __launch_bounds__(192, 1)
         if (!mbar_wait(&empty_bar[s], ph ^ 1u, err, 111)) break;
         mbar_arrive_expect_tx(&full_bar[s], PCfg::STAGE_BYTES);
         const int kx = (kb_first + kb) * PCfg::BK;
-        tma_load_2d(sA_hi(s), &tmAh, kx, m0, &full_bar[s]);
-        tma_load_2d(sA_lo(s), &tmAl, kx, m0, &full_bar[s]);
+        tma_load_2d(sA_hi(s), &tmAh, kx, arow0, &full_bar[s]);
+        tma_load_2d(sA_lo(s), &tmAl, kx, arow0, &full_bar[s]);
         tma_load_2d(sB_hi(s), &tmBh, kx, n0, &full_bar[s]);
         tma_load_2d(sB_lo(s), &tmBl, kx, n0, &full_bar[s]);
       }
@@ -549,8 +572,8 @@ int upload_table(bh_plan* p, const std::vector<double>& radial, int n_r2, const 
   UT_TRY(cudaMemcpy(d_ang, angular.data(), sizeof(double) * angular.size(), cudaMemcpyHostToDevice));
   UT_TRY(cudaMemcpy(d_r2, vox_r2.data(), sizeof(int) * vox_r2.size(), cudaMemcpyHostToDevice));
   UT_TRY(cudaMemcpy(d_ci, colinfo.data(), sizeof(int2) * colinfo.size(), cudaMemcpyHostToDevice));
-  dim3 grid((p->V_pad + 255) / 256, p->Nb_pad);
-  k_build_table<<<grid, 256>>>(d_rad, n_r2, d_ang, d_r2, d_ci, h3, p->V, p->V_pad, p->Nb, p->d_T32, p->d_Thi,
+  dim3 grid((p->VF_pad + 255) / 256, p->Nb_pad);
+  k_build_table<<<grid, 256>>>(d_rad, n_r2, d_ang, d_r2, d_ci, h3, p->VF, p->VF_pad, p->d_T32, p->d_Thi,
                                p->d_Tlo);
   UT_TRY(cudaGetLastError());
   UT_TRY(cudaDeviceSynchronize());
@@ -591,12 +614,13 @@ static int encode_bf16_2d(CUtensorMap* tm, const void* base, uint64_t inner, uin
 }
 
 int make_tensor_maps(bh_plan* p) {
-  // Operands are K-major: inner dimension = V_pad (multiple of 64), boxes 64 x rows.
+  // Operands are K-major: inner dimension = VF_pad (multiple of 64), boxes 64 x rows; the projected volumes
+  // are 8 class blocks of M_cap rows.
   int st;
-  if ((st = encode_bf16_2d(&p->tm_xhi, p->d_Xhi, p->V_pad, p->M_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
-  if ((st = encode_bf16_2d(&p->tm_xlo, p->d_Xlo, p->V_pad, p->M_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
-  if ((st = encode_bf16_2d(&p->tm_thi, p->d_Thi, p->V_pad, p->Nb_pad, kGemmBK, p->gemm_bn)) != BH_OK) return st;
-  if ((st = encode_bf16_2d(&p->tm_tlo, p->d_Tlo, p->V_pad, p->Nb_pad, kGemmBK, p->gemm_bn)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_xhi, p->d_Xhi, p->VF_pad, 8ull * p->M_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_xlo, p->d_Xlo, p->VF_pad, 8ull * p->M_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_thi, p->d_Thi, p->VF_pad, p->Nb_pad, kGemmBK, p->gemm_bn)) != BH_OK) return st;
+  if ((st = encode_bf16_2d(&p->tm_tlo, p->d_Tlo, p->VF_pad, p->Nb_pad, kGemmBK, p->gemm_bn)) != BH_OK) return st;
   return BH_OK;
 }
 
@@ -616,8 +640,8 @@ int set_gemm_bn(bh_plan* p, int bn) {
 // Split-K count of a pass: one GEMM CTA is resident per SM, so take the fewest splits whose last wave of
 // CTAs is at least 90 % full (else the fullest), keeping at least 32 K-blocks per split.
 static int choose_splits(const bh_plan* p, int Mp) {
-  const int tiles = (Mp / kGemmBM) * (p->Nb_pad / 128);
-  const int num_kb = p->V_pad / kGemmBK;
+  const int tiles = (Mp / kGemmBM) * (p->Nb_pad / kGemmBN);
+  const int num_kb = p->VF_pad / kGemmBK;
   const int smax = std::max(1, std::min(p->ksplit_max, num_kb / 32));
   int best = 1;
   double best_eff = 0.0;
@@ -652,70 +676,85 @@ static int launch_to_complex(const bh_plan* p, const float* C, int rows, float* 
   return BH_OK;
 }
 
-static int launch_gemm(bh_plan* p, int Mp, int splits, cudaStream_t stream) {
-  const size_t stride = (size_t)p->M_cap * p->Nb_pad;
+// K splits that hold work for a GEMM of `splits` requested splits (the last ones may be empty).
+static int used_splits(const bh_plan* p, int splits) {
   if (p->mode == BH_MODE_FP32) {
-    const int k_split = round_up((p->V_pad + splits - 1) / splits, SG_BK);
-    dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN, (p->V_pad + k_split - 1) / k_split);  // every split has K work
-    k_sgemm_nt<<<grid, 256, 0, stream>>>(p->d_X32, p->d_T32, p->d_C, Mp, p->Nb_pad, p->V_pad, k_split, stride);
+    const int ks = round_up((p->VF_pad + splits - 1) / splits, SG_BK);
+    return (p->VF_pad + ks - 1) / ks;
+  }
+  const int nkb = p->VF_pad / kGemmBK;
+  const int kbs = round_up((nkb + splits - 1) / splits, KCHUNK);
+  return (nkb + kbs - 1) / kbs;
+}
+
+// The folded GEMM of Mp rows: X holds 8 class blocks of cls_rows rows (X32, or the tensor maps of its BF16
+// hi/lo parts), C gets `splits` partial products split_stride floats apart.
+static int launch_gemm(bh_plan* p, const float* X32, const CUtensorMap& tm_hi, const CUtensorMap& tm_lo, float* C,
+                       int Mp, int splits, int cls_rows, size_t split_stride, cudaStream_t stream) {
+  ClassMap cm = p->cls;
+  cm.rows = cls_rows;
+  if (p->mode == BH_MODE_FP32) {
+    const int k_split = round_up((p->VF_pad + splits - 1) / splits, SG_BK);
+    dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN, (p->VF_pad + k_split - 1) / k_split);  // every split has K work
+    k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, C, Mp, p->Nb_pad, p->VF_pad, k_split, split_stride, cm);
     BH_CHECK_LAUNCH();
     return BH_OK;
   }
-  const int num_kb = p->V_pad / kGemmBK;
+  const int num_kb = p->VF_pad / kGemmBK;
   const int kb_split = round_up((num_kb + splits - 1) / splits, KCHUNK);
   static SmemAttr attr;
   const int st = ensure_smem(k_gemm_tc_promoted, attr, PCfg::SMEM);
   if (st != BH_OK) return st;
   dim3 grid(Mp / kGemmBM, p->Nb_pad / PBN, (num_kb + kb_split - 1) / kb_split);
-  k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(p->tm_xhi, p->tm_xlo, p->tm_thi, p->tm_tlo, p->d_C,
-                                                      p->Nb_pad, num_kb, kb_split, stride, p->d_err);
+  k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, C, p->Nb_pad, num_kb,
+                                                      kb_split, split_stride, p->d_err, cm);
   BH_CHECK_LAUNCH();
   return BH_OK;
 }
 
-// Expansion through caller-provided scratch (used by the entry point that allocates nothing): the same
-// kernels as bh_expand, with the gathered volumes and the real GEMM output placed in `scratch_x` /
-// `scratch_c`, `rows_cap` rows (a multiple of the 128-row M tile) per pass.  Tensor maps of the gathered
-// volumes are encoded for the given scratch on every call (host-side encoding, no allocation).
+// Octant projection of Bc volumes into class blocks of cls_rows rows (from vols, or from the address table
+// vptr).
+static int launch_project(const bh_plan* p, const float* vols, const float* const* vptr, int Bc, int Mp, float* X32,
+                          __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, int cls_rows, cudaStream_t stream) {
+  dim3 g1((p->VF_pad + 255) / 256, Mp);
+  const size_t cls_stride = (size_t)cls_rows * p->VF_pad;
+  if (vptr)
+    k_project<true><<<g1, 256, 0, stream>>>(nullptr, vptr, Bc, p->N, p->d_fund, p->VF, p->VF_pad, cls_stride, X32, Xhi,
+                                            Xlo);
+  else
+    k_project<false><<<g1, 256, 0, stream>>>(vols, nullptr, Bc, p->N, p->d_fund, p->VF, p->VF_pad, cls_stride, X32,
+                                             Xhi, Xlo);
+  BH_CHECK_LAUNCH();
+  return BH_OK;
+}
+
+// Expansion through caller-provided scratch (used by the entry point that allocates nothing and by the
+// serving batches): the same kernels as bh_expand, with the projected volumes (8 class blocks of rows_cap
+// rows) and the real GEMM output placed in `scratch_x` / `scratch_c`, `rows_cap` rows (a multiple of the
+// 128-row M tile) per pass.  Tensor maps of the projected volumes are encoded for the given scratch on
+// every call (host-side encoding, no allocation).
 int expand_into(bh_plan* p, const float* vols, const float* const* vptr, int B, float* coeffs, void* scratch_x,
                 float* scratch_c, int rows_cap, cudaStream_t stream) {
   const long long N3 = (long long)p->N * p->N * p->N;
   float* X32 = nullptr;
   __nv_bfloat16 *Xhi = nullptr, *Xlo = nullptr;
-  CUtensorMap tm_hi, tm_lo;
+  CUtensorMap tm_hi{}, tm_lo{};
   if (p->mode == BH_MODE_FP32) {
     X32 = static_cast<float*>(scratch_x);
   } else {
     Xhi = static_cast<__nv_bfloat16*>(scratch_x);
-    Xlo = Xhi + (size_t)rows_cap * p->V_pad;
+    Xlo = Xhi + (size_t)8 * rows_cap * p->VF_pad;
     int st;
-    if ((st = encode_bf16_2d(&tm_hi, Xhi, p->V_pad, rows_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
-    if ((st = encode_bf16_2d(&tm_lo, Xlo, p->V_pad, rows_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+    if ((st = encode_bf16_2d(&tm_hi, Xhi, p->VF_pad, 8ull * rows_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
+    if ((st = encode_bf16_2d(&tm_lo, Xlo, p->VF_pad, 8ull * rows_cap, kGemmBK, kGemmBM)) != BH_OK) return st;
   }
   for (int b0 = 0; b0 < B; b0 += rows_cap) {
     const int Bc = std::min(rows_cap, B - b0);
     const int Mp = round_up(Bc, kGemmBM);
-    dim3 g1((p->V_pad / 4 + 255) / 256, Mp);
-    if (vptr)
-      k_gather4<true><<<g1, 256, 0, stream>>>(nullptr, vptr + b0, Bc, N3, p->d_vox, p->V, p->V_pad, X32, Xhi, Xlo);
-    else
-      k_gather4<false><<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, nullptr, Bc, N3, p->d_vox, p->V, p->V_pad, X32,
-                                               Xhi, Xlo);
-    BH_CHECK_LAUNCH();
-    if (p->mode == BH_MODE_FP32) {
-      dim3 grid(Mp / SG_BM, p->Nb_pad / SG_BN);
-      k_sgemm_nt<<<grid, 256, 0, stream>>>(X32, p->d_T32, scratch_c, Mp, p->Nb_pad, p->V_pad, p->V_pad, 0);
-    } else {
-      const int num_kb = p->V_pad / kGemmBK;
-      static SmemAttr attr;
-      const int st = ensure_smem(k_gemm_tc_promoted, attr, PCfg::SMEM);
-      if (st != BH_OK) return st;
-      dim3 grid(Mp / kGemmBM, p->Nb_pad / PBN);
-      k_gemm_tc_promoted<<<grid, 192, PCfg::SMEM, stream>>>(tm_hi, tm_lo, p->tm_thi, p->tm_tlo, scratch_c, p->Nb_pad,
-                                                          num_kb, num_kb, 0, p->d_err);
-    }
-    BH_CHECK_LAUNCH();
-    const int st = launch_to_complex(p, scratch_c, Bc, coeffs + (size_t)b0 * p->Nb * 2, 1, 0, stream);
+    int st = launch_project(p, vptr ? nullptr : vols + (size_t)b0 * N3, vptr ? vptr + b0 : nullptr, Bc, Mp, X32, Xhi,
+                            Xlo, rows_cap, stream);
+    if (st == BH_OK) st = launch_gemm(p, X32, tm_hi, tm_lo, scratch_c, Mp, 1, rows_cap, 0, stream);
+    if (st == BH_OK) st = launch_to_complex(p, scratch_c, Bc, coeffs + (size_t)b0 * p->Nb * 2, 1, 0, stream);
     if (st != BH_OK) return st;
   }
   return BH_OK;
@@ -725,24 +764,18 @@ int expand_into(bh_plan* p, const float* vols, const float* const* vptr, int B, 
 int expand_shifted(bh_plan* p, const float* vols, int B, const int3* d_shifts, int nshift, float* coeffs,
                    cudaStream_t stream) {
   const int total = B * nshift;
+  const size_t stride = (size_t)p->M_cap * p->Nb_pad;
   for (int r0 = 0; r0 < total; r0 += p->max_batch) {
     const int rows = std::min(p->max_batch, total - r0);
     const int Mp = round_up(rows, kGemmBM);
-    dim3 g1((p->V_pad + 255) / 256, Mp);
-    k_gather_shifted<<<g1, 256, 0, stream>>>(vols, B, p->N, p->d_vox, d_shifts, nshift, r0, rows, p->V, p->V_pad,
-                                             p->d_X32, p->d_Xhi, p->d_Xlo);
+    dim3 g1((p->VF_pad + 255) / 256, Mp);
+    k_project_shifted<<<g1, 256, 0, stream>>>(vols, B, p->N, p->d_fund, d_shifts, nshift, r0, rows, p->VF, p->VF_pad,
+                                              (size_t)p->M_cap * p->VF_pad, p->d_X32, p->d_Xhi, p->d_Xlo);
     BH_CHECK_LAUNCH();
     const int splits = choose_splits(p, Mp);
-    int st = launch_gemm(p, Mp, splits, stream);
+    int st = launch_gemm(p, p->d_X32, p->tm_xhi, p->tm_xlo, p->d_C, Mp, splits, p->M_cap, stride, stream);
     if (st != BH_OK) return st;
-    const int nkb = p->V_pad / kGemmBK;
-    const int used = (p->mode == BH_MODE_FP32)
-                         ? (p->V_pad + round_up((p->V_pad + splits - 1) / splits, SG_BK) - 1) /
-                               round_up((p->V_pad + splits - 1) / splits, SG_BK)
-                         : (nkb + round_up((nkb + splits - 1) / splits, KCHUNK) - 1) /
-                               round_up((nkb + splits - 1) / splits, KCHUNK);
-    st = launch_to_complex(p, p->d_C, rows, coeffs + (size_t)r0 * p->Nb * 2, used, (size_t)p->M_cap * p->Nb_pad,
-                           stream);
+    st = launch_to_complex(p, p->d_C, rows, coeffs + (size_t)r0 * p->Nb * 2, used_splits(p, splits), stride, stream);
     if (st != BH_OK) return st;
   }
   return BH_OK;
@@ -805,24 +838,17 @@ extern "C" int bh_expand(bh_plan* p, const float* vols, int B, float* coeffs, vo
   }
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const long long N3 = (long long)p->N * p->N * p->N;
+  const size_t stride = (size_t)p->M_cap * p->Nb_pad;
   for (int b0 = 0; b0 < B; b0 += p->max_batch) {
     const int Bc = std::min(p->max_batch, B - b0);
     const int Mp = round_up(Bc, kGemmBM);
-    dim3 g1((p->V_pad / 4 + 255) / 256, Mp);
-    k_gather4<false><<<g1, 256, 0, stream>>>(vols + (size_t)b0 * N3, nullptr, Bc, N3, p->d_vox, p->V, p->V_pad,
-                                             p->d_X32, p->d_Xhi, p->d_Xlo);
-    BH_CHECK_LAUNCH();
-    const int splits = choose_splits(p, Mp);
-    int st = launch_gemm(p, Mp, splits, stream);
+    int st = launch_project(p, vols + (size_t)b0 * N3, nullptr, Bc, Mp, p->d_X32, p->d_Xhi, p->d_Xlo, p->M_cap,
+                            stream);
     if (st != BH_OK) return st;
-    const int nkb = p->V_pad / kGemmBK;
-    const int used = (p->mode == BH_MODE_FP32)
-                         ? (p->V_pad + round_up((p->V_pad + splits - 1) / splits, SG_BK) - 1) /
-                               round_up((p->V_pad + splits - 1) / splits, SG_BK)
-                         : (nkb + round_up((nkb + splits - 1) / splits, KCHUNK) - 1) /
-                               round_up((nkb + splits - 1) / splits, KCHUNK);
-    st = launch_to_complex(p, p->d_C, Bc, coeffs + (size_t)b0 * p->Nb * 2, used, (size_t)p->M_cap * p->Nb_pad,
-                           stream);
+    const int splits = choose_splits(p, Mp);
+    st = launch_gemm(p, p->d_X32, p->tm_xhi, p->tm_xlo, p->d_C, Mp, splits, p->M_cap, stride, stream);
+    if (st != BH_OK) return st;
+    st = launch_to_complex(p, p->d_C, Bc, coeffs + (size_t)b0 * p->Nb * 2, used_splits(p, splits), stride, stream);
     if (st != BH_OK) return st;
   }
   return BH_OK;

@@ -60,8 +60,9 @@ extern "C" int bh_expand_noalloc(bh_plan* p, const float* vols, int B, float* co
     if (st == BH_OK) st = bh::check_expansion_plan(p);
     if (st != BH_OK) return st;
   }
-  // bytes per row of the 128-row M tile: gathered volume (FP32, or BF16 hi + lo) + real GEMM output (FP32)
-  const size_t row_bytes = (size_t)p->V_pad * 4 + (size_t)p->Nb_pad * 4;
+  // bytes per row of the 128-row M tile: the volume's 8 parity-class projections over the fundamental voxels
+  // (FP32, or BF16 hi + lo) + the real GEMM output (FP32)
+  const size_t row_bytes = (size_t)8 * p->VF_pad * 4 + (size_t)p->Nb_pad * 4;
   const size_t tile_rows = bh::kGemmBM;
   // 256 bytes are held back for the alignment of the GEMM-output region
   int rows_cap = (int)((kStaticScratchBytes - 256) / row_bytes) / (int)tile_rows * (int)tile_rows;
@@ -75,7 +76,7 @@ extern "C" int bh_expand_noalloc(bh_plan* p, const float* vols, int B, float* co
   int st = scratch_address(&base);
   if (st != BH_OK) return st;
   unsigned char* b = static_cast<unsigned char*>(base);
-  const size_t x_bytes = bh::round_up64((int64_t)rows_cap * p->V_pad * 4, 256);
+  const size_t x_bytes = bh::round_up64((int64_t)rows_cap * 8 * p->VF_pad * 4, 256);
   float* c = reinterpret_cast<float*>(b + x_bytes);
   return bh::expand_into(p, vols, nullptr, B, coeffs, b, c, rows_cap, static_cast<cudaStream_t>(stream));
 }

@@ -13,6 +13,17 @@
 //   m < 0:  -h^3 R_lk(r) Pbar_l^|m|(cos theta) sin(|m| phi) -> Im f_hat_kl|m|
 // with R_lk(r) = c_lk j_l(lambda_lk r) and Y_l^m = Pbar_l^m(cos theta) e^{i m phi}; negative orders
 // follow from f_hat_{k,l,-m} = (-1)^m conj(f_hat_klm).
+//
+// Octant folding.  The in-ball voxels (coordinates i - N/2 with squared radius below (N/2)^2) form a set
+// symmetric under the reflections x -> -x, y -> -y, z -> -z (the plane i = 0, at -N/2, lies outside the
+// ball), and every real-form row is even or odd under each of them: odd in x for m > 0 odd and for m < 0
+// with |m| even, odd in y for m < 0, odd in z for l + |m| odd.  So each row belongs to one parity class
+// c = (odd in x) + 2 (odd in y) + 4 (odd in z), and sum_v f(v) psi(v) = sum_u psi(u) G_c(u) over the
+// fundamental voxels u = (x, y, z >= 0), where G_c(u) = 2^{-zeros(u)} sum over the 8 sign images s u of
+// (+-1) f(s u) (the sign odd in the class's odd axes; images that coincide on a zero coordinate counted
+// once).  The table holds the rows class by class, each class padded to the GEMM's 128-column tile, over
+// the fundamental voxels only: one eighth of the voxels, and so one eighth of the multiply-adds and of the
+// table, for the same coefficients up to rounding.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -196,7 +207,7 @@ extern "C" int bh_basis_roots(int Lmax, double lambda_max, int* K, double* lambd
 
 static void free_plan(bh_plan* p) {
   if (!p) return;
-  cudaFree(p->d_vox);
+  cudaFree(p->d_fund);
   cudaFree(p->d_slot);
   cudaFree(p->d_T32);
   cudaFree(p->d_Thi);
@@ -261,26 +272,28 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
   for (int l = 0; l <= p->Lmax + 1; ++l) p->layout.off[l] = p->offs[l];
   for (int l = 0; l <= p->Lmax; ++l) p->layout.K[l] = p->K[l];
 
-  // ---- voxels of the ball, in flat [z][y][x] order
+  // ---- voxels of the ball (counted) and its fundamental voxels x, y, z >= 0 (z-major order)
   const int N = p->N, h = N / 2;
-  std::vector<int> vox, vox_r2;
+  std::vector<int> fund, vox_r2;
   std::vector<int> vx, vy, vz;
-  for (int iz = 0; iz < N; ++iz)
-    for (int iy = 0; iy < N; ++iy)
-      for (int ix = 0; ix < N; ++ix) {
-        const int x = ix - h, y = iy - h, z = iz - h;
+  p->V = 0;
+  for (int z = -h; z < h; ++z)
+    for (int y = -h; y < h; ++y)
+      for (int x = -h; x < h; ++x) p->V += (x * x + y * y + z * z < h * h) ? 1 : 0;
+  for (int z = 0; z < h; ++z)
+    for (int y = 0; y < h; ++y)
+      for (int x = 0; x < h; ++x) {
         const int r2 = x * x + y * y + z * z;
         if (r2 < h * h) {
-          vox.push_back((iz * N + iy) * N + ix);
+          fund.push_back(x | (y << 10) | (z << 20));
           vox_r2.push_back(r2);
           vx.push_back(x);
           vy.push_back(y);
           vz.push_back(z);
         }
       }
-  p->V = (int)vox.size();
-  p->V_pad = round_up(p->V, kPadV);
-  p->Nb_pad = round_up(p->Nb, kPadNb);
+  p->VF = (int)fund.size();
+  p->VF_pad = round_up(p->VF, kPadV);
   p->M_cap = round_up(max_batch, kGemmBM);
 
   // ---- radial table R[lk][r2] = c_lk j_l(lambda_lk sqrt(r2)/h), r2 = 0..h^2-1 (expansion plans only)
@@ -311,7 +324,7 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
 
   // ---- angular table A[lm][v], lm = l^2 + l + m (real form, see header comment)
   const int nlm = (p->Lmax + 1) * (p->Lmax + 1);
-  std::vector<double> angular(match_only ? 0 : (size_t)nlm * p->V);
+  std::vector<double> angular(match_only ? 0 : (size_t)nlm * p->VF);
   if (!match_only) {
     std::vector<std::thread> th;
     const int nth = std::max(1u, std::thread::hardware_concurrency());
@@ -319,7 +332,7 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     for (int t = 0; t < nth; ++t)
       th.emplace_back([&, t] {
         std::vector<double> P((L + 1) * (L + 1));
-        for (int v = t; v < p->V; v += nth) {
+        for (int v = t; v < p->VF; v += nth) {
           const double x = vx[v], y = vy[v], z = vz[v];
           const double r = std::sqrt(x * x + y * y + z * z), rho = std::sqrt(x * x + y * y);
           const double ct = (r > 0) ? z / r : 1.0;
@@ -331,10 +344,10 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
               const double pl = P[l * (L + 1) + m];
               const int base = l * l + l;
               if (m == 0) {
-                angular[(size_t)base * p->V + v] = pl;
+                angular[(size_t)base * p->VF + v] = pl;
               } else {
-                angular[(size_t)(base + m) * p->V + v] = pl * cm;
-                angular[(size_t)(base - m) * p->V + v] = -pl * sm;
+                angular[(size_t)(base + m) * p->VF + v] = pl * cm;
+                angular[(size_t)(base - m) * p->VF + v] = -pl * sm;
               }
             }
             const double cn = cm * cphi - sm * sphi, sn = sm * cphi + cm * sphi;
@@ -346,19 +359,37 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     for (auto& x : th) x.join();
   }
 
-  // ---- per-slot table rows and complex sources
-  std::vector<int2> colinfo(p->Nb);
+  // ---- table rows (real form) grouped by parity class, and the complex sources of every slot
+  std::vector<int> row_class(p->Nb), row_col(p->Nb);
+  int class_count[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int l = 0; l <= p->Lmax; ++l)
+    for (int k = 0; k < p->K[l]; ++k)
+      for (int m = -l; m <= l; ++m) {
+        const int s = p->offs[l] + k * (2 * l + 1) + m + l, mu = m < 0 ? -m : m;
+        const int odd_x = (m >= 0) ? (mu & 1) : !(mu & 1), odd_y = m < 0, odd_z = (l + mu) & 1;
+        row_class[s] = odd_x | (odd_y << 1) | (odd_z << 2);
+        row_col[s] = class_count[row_class[s]]++;
+      }
+  int class_base[8];
+  for (int c = 0, base = 0; c < 8; ++c) {
+    class_base[c] = base;
+    base += round_up(class_count[c], kGemmBN);
+    p->cls.ntile_end[c] = base / kGemmBN;
+  }
+  p->Nb_pad = p->cls.ntile_end[7] * kGemmBN;
+  for (int s = 0; s < p->Nb; ++s) row_col[s] += class_base[row_class[s]];
+  std::vector<int2> colinfo(p->Nb_pad, make_int2(-1, -1));  // padding columns stay zero
   std::vector<int2> slot(p->Nb);
   for (int l = 0, lk = 0; l <= p->Lmax; ++l) {
     for (int k = 0; k < p->K[l]; ++k, ++lk) {
       const int base = p->offs[l] + k * (2 * l + 1);
       for (int m = -l; m <= l; ++m) {
         const int s = base + m + l;
-        colinfo[s] = make_int2(lk, l * l + l + m);
+        colinfo[row_col[s]] = make_int2(lk, l * l + l + m);
         const int mu = m < 0 ? -m : m;
-        const int pos = base + l + mu, neg = base + l - mu;
+        const int pos = row_col[base + l + mu], neg = row_col[base + l - mu];
         if (m == 0) {
-          slot[s] = make_int2(s + 1, 0);
+          slot[s] = make_int2(pos + 1, 0);
         } else if (m > 0) {
           slot[s] = make_int2(pos + 1, neg + 1);
         } else {
@@ -382,14 +413,14 @@ extern "C" int bh_plan_create(bh_plan** out, const bh_plan_opts* o) {
     if (e == cudaSuccess) return BH_OK;
     return fail(e == cudaErrorMemoryAllocation ? BH_ERR_OOM : BH_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   };
-  PLAN_TRY(cuda_ok(cudaMalloc(&p->d_vox, sizeof(int) * p->V), "cudaMalloc vox"));
-  PLAN_TRY(cuda_ok(cudaMemcpy(p->d_vox, vox.data(), sizeof(int) * p->V, cudaMemcpyHostToDevice), "upload vox"));
+  PLAN_TRY(cuda_ok(cudaMalloc(&p->d_fund, sizeof(int) * p->VF), "cudaMalloc fund"));
+  PLAN_TRY(cuda_ok(cudaMemcpy(p->d_fund, fund.data(), sizeof(int) * p->VF, cudaMemcpyHostToDevice), "upload fund"));
   PLAN_TRY(cuda_ok(cudaMalloc(&p->d_slot, sizeof(int2) * p->Nb), "cudaMalloc slot"));
   PLAN_TRY(cuda_ok(cudaMemcpy(p->d_slot, slot.data(), sizeof(int2) * p->Nb, cudaMemcpyHostToDevice), "upload slot"));
   PLAN_TRY(cuda_ok(cudaMalloc(&p->d_err, sizeof(int)), "cudaMalloc err"));
   PLAN_TRY(cuda_ok(cudaMemset(p->d_err, 0, sizeof(int)), "memset err"));
-  const size_t tab_elems = (size_t)p->Nb_pad * p->V_pad;
-  const size_t x_elems = (size_t)p->M_cap * p->V_pad;
+  const size_t tab_elems = (size_t)p->Nb_pad * p->VF_pad;
+  const size_t x_elems = (size_t)8 * p->M_cap * p->VF_pad;  // [class][row][fundamental voxel]
   if (match_only) {
     // no table, gathered volumes or GEMM output
   } else if (p->mode == BH_MODE_FP32) {
@@ -487,6 +518,14 @@ extern "C" int bh_plan_layout(const bh_plan* p, int* Nb, int* V, int* offsets) {
   if (V) *V = p->V;
   if (offsets)
     for (int l = 0; l <= p->Lmax + 1; ++l) offsets[l] = p->offs[l];
+  return BH_OK;
+}
+
+extern "C" int bh_plan_gemm(const bh_plan* p, int* K, int* N) {
+  clear_error();
+  if (!p) return fail(BH_ERR_ARG, "plan is NULL");
+  if (K) *K = p->VF_pad;
+  if (N) *N = p->Nb_pad;
   return BH_OK;
 }
 

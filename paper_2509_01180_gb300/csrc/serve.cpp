@@ -18,6 +18,12 @@
 // overtaken by a later request of the same class); an express request may take a free bulk stream
 // when no bulk request waits.  Off by default: under bursts of large requests the measured p99 latency
 // of the mixed Poisson workload was lower with one class.
+//
+// A request larger than `piece` subtomograms is admitted piece by piece: its first piece is queued at
+// submission, and each time a piece is admitted the next one joins the END of the queue, behind requests
+// that arrived in the meantime, so a burst of large requests no longer holds every stream slot while
+// small ones wait.  Pieces draw the random starts their subtomograms would draw unsplit, so a result does
+// not depend on the split; the request completes with its last piece.
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -61,6 +67,10 @@ struct Req {
   bool express = false;
   Clock::time_point t_submit, t_done;
   int status = BH_PENDING;
+  // a request admitted in pieces: each piece points at its request; the request counts what is left
+  std::shared_ptr<Req> parent;
+  int pieces_left = 0;  // pieces not finished yet
+  int next_off = 0;     // first subtomogram not yet queued as a piece
 };
 
 struct Slot {
@@ -80,12 +90,13 @@ struct Slot {
 };
 
 // Device bytes of a batch: its volumes (unless read in place from the request buffers, then a table of
-// B addresses), coefficients, starts, template indices, results and expansion scratch.
+// B addresses), coefficients, starts, template indices, results and expansion scratch (the 8 parity-class
+// projections of each row over the fundamental voxels, and the real GEMM output).
 size_t batch_bytes(const bh_plan* p, int B, int S, bool in_place) {
   const size_t rows = (size_t)bh::round_up(std::min(B, kScratchRows), bh::kGemmBM);
   const size_t vols = in_place ? (size_t)B * sizeof(void*) : (size_t)B * p->N * p->N * p->N * 4;
   return vols + (size_t)B * p->Nb * 8 + (size_t)B * S * 16 + (size_t)B * 4 + (size_t)B * 20 +
-         rows * ((size_t)p->V_pad * 4 + (size_t)p->Nb_pad * 4) + 4 * 256;
+         rows * ((size_t)8 * p->VF_pad * 4 + (size_t)p->Nb_pad * 4) + 4 * 256;
 }
 
 // Work of one evaluation of Eq. 2 with its gradient at band L (flop): 30 per orbit-step of the
@@ -99,12 +110,12 @@ double eval_flop(int L) {
 
 // Estimated device time (ms) of a batch of B subtomograms: the expansion at 1 PFLOP/s of executed tensor
 // work (three BF16 products) or 40 TFLOP/s (FP32), but no less than one pass of the basis table over HBM
-// (every batch streams it once: 13 GB for the BF16 hi/lo table at 64^3) at 6.5 TB/s; the ascent at
+// (every batch streams it once: 1.8 GB for the folded BF16 hi/lo table at 64^3) at 6.5 TB/s; the ascent at
 // 20 TFLOP/s of FP32 work.  Throughputs measured for these kernels; used only to classify requests.
 double est_ms(const bh_plan* p, const int* stages, int nstages, int steps, int B, int S) {
-  const double gemm = 2.0 * p->V * p->Nb;
+  const double gemm = 2.0 * p->VF_pad * p->Nb_pad;  // the folded GEMM: fundamental voxels x padded table rows
   const double expand = (p->mode == BH_MODE_BF16_SPLIT) ? 3.0 * gemm / 1e12 : gemm / 40e12;
-  const double table = 4.0 * p->Nb_pad * p->V_pad / 6.5e12;  // FP32, or BF16 hi + lo: 4 bytes per entry
+  const double table = 4.0 * p->Nb_pad * p->VF_pad / 6.5e12;  // FP32, or BF16 hi + lo: 4 bytes per entry
   double align = 0.0;
   for (int i = 0; i < nstages; ++i) align += eval_flop(stages[i]);
   align *= (double)S * (1.0 + steps) / 20e12;
@@ -217,7 +228,7 @@ int launch_batch(bh_server* s, Slot& sl, int N, int S) {
   BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_tidx, (size_t)B * 4, pool, st));
   BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_quat, (size_t)B * 16, pool, st));
   BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_score, (size_t)B * 4, pool, st));
-  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_sx, (size_t)rows * p->V_pad * 4, pool, st));
+  BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_sx, (size_t)rows * 8 * p->VF_pad * 4, pool, st));
   BH_CUDA_TRY(cudaMallocFromPoolAsync((void**)&d_sc, (size_t)rows * p->Nb_pad * 4, pool, st));
   off = 0;
   for (auto& r : sl.reqs) {
@@ -264,12 +275,48 @@ void retire(bh_server* s, Slot& sl, int status) {
     off += r->r.B;
     r->t_done = now;
     r->status = status;
-    ++s->completed;
+    if (r->parent) {  // a piece: its outputs were written into the request's arrays
+      Req& q = *r->parent;
+      if (status != BH_OK) q.status = status;
+      if (--q.pieces_left == 0) {
+        q.t_done = now;
+        if (q.status == BH_PENDING) q.status = BH_OK;
+        ++s->completed;
+      }
+    } else {
+      ++s->completed;
+    }
   }
   sl.reqs.clear();
   sl.busy = false;
   s->used -= sl.bytes;
   sl.bytes = 0;
+}
+
+// The next piece of request q (caller holds s->mu): at most `piece` subtomograms from q.next_off on, with
+// the request's arrays offset and, for random starts, the seed offset so that the piece draws the starts
+// its subtomograms would draw unsplit (bh_random_starts counter seed + 3 (b S + s)).
+std::shared_ptr<Req> next_piece(bh_server* s, const std::shared_ptr<Req>& q) {
+  const int off = q->next_off, n = std::min(s->o.piece, q->r.B - off);
+  const size_t N3 = (size_t)q->N * q->N * q->N;
+  auto pc = std::make_shared<Req>();
+  pc->ticket = 0;
+  pc->r = q->r;
+  pc->r.B = n;
+  pc->r.vols = q->r.vols + (size_t)off * N3;
+  pc->r.quat_out = q->r.quat_out + (size_t)off * 4;
+  pc->r.score_out = q->r.score_out + off;
+  if (q->r.starts)
+    pc->r.starts = q->r.starts + (size_t)off * q->r.S * 4;
+  else
+    pc->r.seed = q->r.seed + 3ull * (uint64_t)off * (uint64_t)q->r.S;
+  pc->N = q->N;
+  pc->row = q->row;
+  pc->express = q->express;
+  pc->t_submit = q->t_submit;
+  pc->parent = q;
+  q->next_off = off + n;
+  return pc;
 }
 
 void worker_loop(bh_server* s) {
@@ -326,6 +373,7 @@ void worker_loop(bh_server* s) {
         const Box& box = s->boxes[N];
         bh_plan* p = box.plan;
         std::vector<std::shared_ptr<Req>> take;
+        std::vector<std::shared_ptr<Req>> next_pieces;
         int B = 0;
         for (auto it = s->queue.begin(); it != s->queue.end();) {
           auto& r = *it;
@@ -340,6 +388,7 @@ void worker_loop(bh_server* s) {
           if (fits) {
             B += r->r.B;
             take.push_back(r);
+            if (r->parent && r->parent->next_off < r->parent->r.B) next_pieces.push_back(next_piece(s, r->parent));
             it = s->queue.erase(it);
           } else if (take.empty()) {
             break;  // the class head does not fit yet: keep its arrival order
@@ -347,6 +396,7 @@ void worker_loop(bh_server* s) {
             ++it;
           }
         }
+        for (auto& pc : next_pieces) s->queue.push_back(pc);  // behind everything that arrived meanwhile
         if (take.empty()) continue;
         free_slot->busy = true;
         free_slot->reqs = take;
@@ -409,6 +459,8 @@ extern "C" int bh_serve_create(bh_server** out, const bh_serve_opts* o) {
   if (opts.steps == 0) opts.steps = 30;
   if (opts.ingest != 0 && opts.ingest != 1) return fail(BH_ERR_ARG, "ingest %d not in {0,1}", opts.ingest);
   if (opts.express_ms == 0.0) opts.express_ms = 2.0;
+  if (opts.piece == 0) opts.piece = 128;
+  if (opts.piece < 1) return fail(BH_ERR_ARG, "piece %d", opts.piece);
   if (opts.max_inflight < 1 || opts.max_inflight > 16) return fail(BH_ERR_ARG, "max_inflight %d", opts.max_inflight);
   if (opts.max_batch < 1 || opts.max_batch > 65536) return fail(BH_ERR_ARG, "max_batch %d", opts.max_batch);
   if (opts.queue_capacity < 1) return fail(BH_ERR_ARG, "queue_capacity %d", opts.queue_capacity);
@@ -540,9 +592,14 @@ extern "C" int bh_serve_submit(bh_server* s, const bh_request* r, uint64_t* tick
   q->row = t.row;
   const Box& box = s->boxes[t.N];
   q->express = s->o.express_slots > 0 &&
-               est_ms(p, box.stages, box.nstages, s->o.steps, r->B, r->S) <= s->express_ms;
+               est_ms(p, box.stages, box.nstages, s->o.steps, std::min(r->B, s->o.piece), r->S) <= s->express_ms;
   q->t_submit = Clock::now();
-  s->queue.push_back(q);
+  if (r->B > s->o.piece) {  // admitted piece by piece; the first piece is queued now
+    q->pieces_left = (r->B + s->o.piece - 1) / s->o.piece;
+    s->queue.push_back(next_piece(s, q));
+  } else {
+    s->queue.push_back(q);
+  }
   s->reqs[q->ticket] = q;
   ++s->submitted;
   *ticket = q->ticket;
@@ -617,7 +674,10 @@ extern "C" int bh_serve_destroy(bh_server* s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
-    for (auto& q : s->queue) q->status = BH_ERR_ARG;
+    for (auto& q : s->queue) {
+      q->status = BH_ERR_ARG;
+      if (q->parent) q->parent->status = BH_ERR_ARG;
+    }
     s->queue.clear();
     s->cv_work.notify_all();
   }

@@ -179,3 +179,26 @@ def test_express_and_in_place_give_the_batch_results():
         if not kw.get("express_slots"):
             assert st["express_batches"] == 0
         assert st["staging_allocs"] >= 2 and st["launch_ms_max"] >= 0.0
+
+
+def test_pieces_give_the_unsplit_results():
+    """A request admitted in pieces (each next piece queued behind later arrivals) returns bitwise what the
+    same request returns unsplit: every subtomogram keeps its own random starts."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    tpl = synth.render(16, synth.blob_template(synth.rng_for(9, 11), 20, 1.2, 6.0)).astype(np.float32)
+    vols = vols_for(16, 70, 3)
+    out = []
+    for piece in (16, 1024):
+        s = bh.bh_serve_create(hbm_budget_bytes=1 << 30, max_inflight=3, max_batch=256, steps=10, piece=piece)
+        tid = s.add_template(tpl)
+        small = [s.submit(tid, vols_for(16, 3, 40 + i), S=8, seed=i) for i in range(3)]
+        q, sc, _ = s.wait(s.submit(tid, vols, S=8, seed=5), timeout_ms=120000)
+        for t in small:
+            s.wait(t, timeout_ms=120000)
+        st = s.stats()
+        out.append((q, sc, st["batches"], st["completed"]))
+        s.destroy()
+    (q1, s1, b1, c1), (q2, s2, b2, c2) = out
+    assert np.array_equal(q1, q2) and np.array_equal(s1, s2)
+    assert b1 >= 5 and c1 == c2 == 4  # 70 subtomograms in pieces of 16; completions count requests
