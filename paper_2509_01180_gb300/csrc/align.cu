@@ -496,40 +496,35 @@ __device__ void eval_flat(const float4* __restrict__ tab, int Lb, int L, const f
       }
     }
     // l = m_hi+1 .. L: every live lane is inside its orbit
-    // four bands per iteration (a loop branch per four steps), then single steps
+    // two bands per iteration, the next pair's constants fetched one iteration ahead; then a last single step
     const float4* ep = ep0 + (m_hi + 1 - m) * wl;
     int l = m_hi + 1;
-    for (; l + 3 <= L; l += 4) {
-      const float4 x0 = ep[0], x1 = ep[wl], x2 = ep[2 * wl], x3 = ep[3 * wl];
-      ep += 4 * wl;
-      const float4 k0 = c_ecoef[l], k1 = c_ecoef[l + 1], k2 = c_ecoef[l + 2], k3 = c_ecoef[l + 3];
+    float4 k0 = c_ecoef[l], k1 = c_ecoef[l + 1];
+    for (; l + 1 <= L; l += 2) {
+      const float4 x0 = ep[0], x1 = ep[wl];
+      ep += 2 * wl;
+      const float4 kn0 = c_ecoef[l + 2], kn1 = c_ecoef[l + 3];
       const float g0 = gcoef(k0, sq2, pq2), g1 = gcoef(k1, sq2, pq2);
-      const float g2 = gcoef(k2, sq2, pq2), g3 = gcoef(k3, sq2, pq2);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        float ea, pa, eb, pb, ec, pc, ee, pe;
+        float ea, pa, eb, pb;
         BH_FSTEP(j, ea, pa, e1[j], e2[j], p1[j], p2[j], k0, g0, x0);
         BH_FACC(j, ea, pa, x0);
         BH_FSTEP(j, eb, pb, ea, e1[j], pa, p1[j], k1, g1, x1);
         BH_FACC(j, eb, pb, x1);
-        BH_FSTEP(j, ec, pc, eb, ea, pb, pa, k2, g2, x2);
-        BH_FACC(j, ec, pc, x2);
-        BH_FSTEP(j, ee, pe, ec, eb, pc, pb, k3, g3, x3);
-        BH_FACC(j, ee, pe, x3);
-        e2[j] = ec; e1[j] = ee; p2[j] = pc; p1[j] = pe;
+        e2[j] = ea; e1[j] = eb; p2[j] = pa; p1[j] = pb;
       }
+      k0 = kn0;
+      k1 = kn1;
     }
-    for (; l <= L; ++l) {
+    if (l <= L) {
       const float4 x0 = ep[0];
-      ep += wl;
-      const float4 k0 = c_ecoef[l];
       const float g0 = gcoef(k0, sq2, pq2);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         float ea, pa;
         BH_FSTEP(j, ea, pa, e1[j], e2[j], p1[j], p2[j], k0, g0, x0);
         BH_FACC(j, ea, pa, x0);
-        e2[j] = e1[j]; e1[j] = ea; p2[j] = p1[j]; p1[j] = pa;
       }
     }
 #undef BH_FSTEP
