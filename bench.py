@@ -49,10 +49,13 @@ def align_source_sha() -> str:
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the ascent kernel from an ncu
-# capture, by (workload, subtomograms per launch, lanes per start, starts per thread), with the hash of
-# align.cu the capture was taken on; captures of a smaller batch are scaled by the subtomogram count
-# (the traffic is the coefficients and starts read once).  Other shapes, or another source, report null.
-ALIGN_TRAFFIC_BYTES = {}
+# capture, by (workload, lanes per start, starts per thread, orbit dealing): (bytes, subtomograms in the
+# captured launch, hash of align.cu the capture was taken on).  A capture of a smaller batch is scaled by
+# the subtomogram count (the kernel reads each subtomogram's coefficients and starts once); the figure is
+# used only while the hash matches.
+ALIGN_TRAFFIC_BYTES = {
+    ("precision64", 16, 2, 2): (195_439_360 + 3_302_144, 1024, "4202a7a2c3f49f68"),
+}
 
 
 def describe(w) -> str:

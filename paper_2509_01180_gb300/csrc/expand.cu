@@ -153,17 +153,26 @@ __global__ void k_to_complex(const float* __restrict__ C, int ldc, int B, int Nb
 }
 
 // The same, one CTA per row: the row's split partial sums are added (in split order) into shared memory with
-// coalesced loads, then the complex coefficients are formed from shared memory.  Bitwise equal to
-// k_to_complex (a negated sum equals the sum of the negated terms).
+// coalesced 16-byte loads (ldc and split_stride are multiples of 4 floats), then the complex coefficients are
+// formed from shared memory.  Bitwise equal to k_to_complex (a negated sum equals the sum of the negated terms).
 __global__ void __launch_bounds__(256) k_to_complex_rows(const float* __restrict__ C, int ldc, int Nb,
                                                          const int2* __restrict__ slot, float2* __restrict__ out,
                                                          int splits, size_t split_stride) {
-  extern __shared__ float row[];
+  extern __shared__ float4 row4[];
+  const float* row = reinterpret_cast<const float*>(row4);
   const int b = blockIdx.x;
-  for (int c = threadIdx.x; c < ldc; c += blockDim.x) {
-    float v = 0.f;
-    for (int z = 0; z < splits; ++z) v += C[(size_t)z * split_stride + (size_t)b * ldc + c];
-    row[c] = v;
+  const int n4 = ldc / 4;
+#pragma unroll 4
+  for (int c = threadIdx.x; c < n4; c += blockDim.x) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int z = 0; z < splits; ++z) {
+      const float4 t = reinterpret_cast<const float4*>(C + (size_t)z * split_stride + (size_t)b * ldc)[c];
+      v.x += t.x;
+      v.y += t.y;
+      v.z += t.z;
+      v.w += t.w;
+    }
+    row4[c] = v;
   }
   __syncthreads();
   for (int s = threadIdx.x; s < Nb; s += blockDim.x) {
@@ -661,9 +670,9 @@ static int choose_splits(const bh_plan* p, int Mp) {
 static int launch_to_complex(const bh_plan* p, const float* C, int rows, float* coeffs, int splits, size_t stride,
                              cudaStream_t stream) {
   const size_t row_bytes = (size_t)p->Nb_pad * sizeof(float);
-  if (row_bytes <= 96 * 1024) {
+  if (row_bytes <= 200 * 1024) {
     static SmemAttr attr;
-    const int st = ensure_smem(k_to_complex_rows, attr, 96 * 1024);
+    const int st = ensure_smem(k_to_complex_rows, attr, row_bytes);
     if (st != BH_OK) return st;
     k_to_complex_rows<<<rows, 256, row_bytes, stream>>>(C, p->Nb_pad, p->Nb, p->d_slot, reinterpret_cast<float2*>(coeffs),
                                                         splits, stride);
