@@ -248,9 +248,10 @@ typedef struct {
   int starts_per_thread;  /* 0 = autotuned; 1, or 2 (S even: each thread advances two starts' recursions
                              through every orbit, sharing the table loads and coefficients) */
   int refine_fp64;        /* K in 0..64: after the FP32 ascent, re-score the K best starts (by FP32
-                             score) at the last band with the d-recursion, seeds, phases and sums in
-                             FP64 and select among them on the FP64 score (score_out then holds it,
-                             rounded to float).  Needs start_quat_out and start_score_out.  0 = off */
+                             score) at the last band with the d-recursion, seeds and phases in FP64
+                             and the chain sums in compensated FP32 pairs (see bh_refine_fp64), and
+                             select among them on that score (score_out then holds it, rounded to
+                             float).  Needs start_quat_out and start_score_out.  0 = off */
   int newton;             /* 0: gradient ascent (Sec. II-C).  1: damped Newton steps (Sec. III): per
                              iteration, d = -H^{-1} g when -H is positive definite, else the gradient
                              step pi/(2L) g/|g|; d clipped to length pi/L and scaled by a damping factor
@@ -303,9 +304,13 @@ int bh_align_batch(const bh_plan* plan, const float* tmpl, const float* sub, int
 /*
  * The precision form's final refinement as a call of its own (bh_align_batch runs the same step when
  * opts->refine_fp64 = K): for every subtomogram, the K starts with the largest FP32 scores in
- * start_score (ties: lowest index) are scored at band L with the d-recursion, seeds, phases and sums in
- * FP64 (Eq. 2; the orbit table of P_l xi^l is rounded to FP32 once per entry), and the best of them on
- * the FP64 score is written to quat_out / score_out (rounded to float) / score64_out.
+ * start_score (ties: lowest index) are scored at band L with the d-recursion, seeds and phases in FP64
+ * (Eq. 2; the orbit table of P_l xi^l is rounded to FP32 once per entry).  Each orbit's sum over l of
+ * recursion value times table entry is accumulated as an FP32 pair (the FP64 value split into two FP32
+ * parts, products split exactly, error-free two-sums: within about 2^-43 of the sum of the terms'
+ * magnitudes, against about 2^-48 for FP64 summation of a 33-term chain and 2^-24 for the table's own FP32
+ * rounding), then combined with the phases in FP64.  The best of the K on that score is
+ * written to quat_out / score_out (rounded to float) / score64_out.
  *   start_quat   device, B * S * 4 floats: final rotation of every start (opts->start_quat_out)
  *   start_score  device, B * S floats: their FP32 scores (opts->start_score_out)
  *   L            band, 0..Lmax;  K  1..min(64, S)

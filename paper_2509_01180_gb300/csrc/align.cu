@@ -1431,6 +1431,36 @@ __device__ __forceinline__ Rot64 rot64(float4 qf) {
   return r;
 }
 
+// v (FP64) as hi + lo with hi, lo FP32: hi keeps the sign, exponent and leading 24 significand bits of v
+// (truncation, formed with integer operations), lo the same of the exact remainder v - hi, so that
+// |v - hi - lo| <= 2^-46 |v|.  Values outside the FP32 normal range (|v| < 2^-126 or >= 2^128) give
+// hi = lo = 0.  Costs one FP64 subtraction; the conversions run on the integer pipe, not the FP64 one.
+__device__ __forceinline__ float trunc_float(double v, double* vt) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int h = (unsigned int)(b >> 32);
+  const int e = (int)((h >> 20) & 0x7FFu) - 896;  // FP32 biased exponent
+  const bool ok = e > 0 && e < 255;
+  const unsigned int fb = (h & 0x80000000u) | ((unsigned int)e << 23) | ((h & 0xFFFFFu) << 3) | ((unsigned int)b >> 29);
+  *vt = ok ? __longlong_as_double((long long)(b & 0xFFFFFFFFE0000000ull)) : 0.0;
+  return ok ? __uint_as_float(fb) : 0.f;
+}
+__device__ __forceinline__ void split64(double v, float& hi, float& lo) {
+  double vh, vl;
+  hi = trunc_float(v, &vh);
+  lo = trunc_float(v - vh, &vl);
+}
+// s + c += (hi + lo) x, compensated: hi x is split exactly into p + pe (FMA), p is added to s with an
+// error-free two-sum, and the two-sum's error, pe and lo x go to the correction c.
+__device__ __forceinline__ void acc_ff(float& s, float& c, float hi, float lo, float x) {
+  const float p = hi * x;
+  const float pe = fmaf(hi, x, -p);
+  const float t = s + p;
+  const float z = t - s;
+  const float err = (s - (t - z)) + (p - z);
+  s = t;
+  c = fmaf(lo, x, c + (err + pe));
+}
+
 // FP64 score of one rotation at band L, NL lanes per rotation (NL > 32: several warps; the caller adds the
 // per-warp partial sums).  Orbits are dealt by their flat index: lane q takes (m, n) with
 // m^2 + m + n = q mod NL, so rows shorter than NL still spread over all lanes.  The lane's first orbit in
@@ -1457,8 +1487,20 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
       d = ((m - n) & 1) ? -d : d;
       const float4* ep = rowp + (n + m);
       const double2* kp = crow + (n + m);
+      // the chain's sums a = sum_l e^l x^l: the recursion in FP64, each term accumulated in compensated FP32
+      // (s + c; the split of e^l loses 2^-46 of it, the sum about 2^-43 of the terms' magnitudes, far below the
+      // table's FP32 rounding), without FP64 conversions and multiply-adds of the FP32 table entries
       float4 xv = *ep;
-      double a1r = d * xv.x, a1i = d * xv.y, a2r = d * xv.z, a2i = d * xv.w;
+      float s1r, s1i, s2r, s2i, c1r = 0.f, c1i = 0.f, c2r = 0.f, c2i = 0.f;
+      {
+        float hi, lo;
+        split64(d, hi, lo);
+        s1r = s1i = s2r = s2i = 0.f;
+        acc_ff(s1r, c1r, hi, lo, xv.x);
+        acc_ff(s1i, c1i, hi, lo, xv.y);
+        acc_ff(s2r, c2r, hi, lo, xv.z);
+        acc_ff(s2i, c2i, hi, lo, xv.w);
+      }
       double e1 = d, e2 = 0.0;
       for (int l = m + 1; l <= L; ++l) {
         ep += w2;
@@ -1468,11 +1510,15 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
         e2 = e1;
         e1 = en;
         xv = *ep;
-        a1r = fma(en, (double)xv.x, a1r);
-        a1i = fma(en, (double)xv.y, a1i);
-        a2r = fma(en, (double)xv.z, a2r);
-        a2i = fma(en, (double)xv.w, a2i);
+        float hi, lo;
+        split64(en, hi, lo);
+        acc_ff(s1r, c1r, hi, lo, xv.x);
+        acc_ff(s1i, c1i, hi, lo, xv.y);
+        acc_ff(s2r, c2r, hi, lo, xv.z);
+        acc_ff(s2i, c2i, hi, lo, xv.w);
       }
+      const double a1r = (double)s1r + (double)c1r, a1i = (double)s1i + (double)c1i;
+      const double a2r = (double)s2r + (double)c2r, a2i = (double)s2i + (double)c2i;
       S += (P1.x * a1r - P1.y * a1i) + (P2.x * a2r - P2.y * a2i);
       P1 = cm64(P1, R1);
       P2 = cm64(P2, R2);
@@ -1485,7 +1531,8 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
 }
 
 // Top-K re-scoring in FP64 at the last band (optional): the K starts with the largest FP32 final score
-// (ties: lowest index) are re-evaluated with the d-recursion, seeds, phases and sums in FP64 (the table's
+// (ties: lowest index) are re-evaluated with the d-recursion, seeds and phases in FP64, the chain sums in
+// compensated FP32 pairs (score_rotation64; the table's
 // xi stays the FP32 product; the rational recursion coefficients come from the plan's FP64 table), and
 // the subtomogram's result is the best of them on the FP64 score.  One CTA of K * NL threads per
 // subtomogram; shared memory: the orbit table, then the per-start power tables A^j, Bc^j (j < NL).
