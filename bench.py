@@ -369,26 +369,30 @@ def run_workload(args, w, rank, world, device, *, refine: int, sec3: bool, wedge
         q_res = quat.cpu().numpy().astype(np.float64)
 
         # end to end through the public API: every step copies its volumes from pinned host memory and
-        # reads its rotations and scores back.  Two device input buffers: the copy of step k+1 (copy
-        # stream) overlaps the expansion and alignment of step k (compute stream); a buffer is refilled
-        # only after the expansion that read it has finished.  Timed from the first timed copy to the last
-        # read-back.
+        # reads its rotations and scores back.  Three device input buffers: the copies of steps k+1 and
+        # k+2 (copy stream) overlap the expansion and alignment of step k (compute stream), so that a host
+        # copy slowed by other traffic on the host (measured: most 4.3 GB copies take 20 ms, a few up to
+        # 190 ms) still finishes before its step; a buffer is refilled only after the expansion that read
+        # it has finished.  Timed from the first timed copy to the last read-back.
         hv = torch.from_numpy(w.vols).pin_memory()
         hq = [torch.empty((B, 4), dtype=torch.float32).pin_memory() for _ in range(2)]
         hs = [torch.empty((B,), dtype=torch.float32).pin_memory() for _ in range(2)]
-        dv = [vols, torch.empty_like(vols)]
+        dv = [vols, torch.empty_like(vols), torch.empty_like(vols)]
         cstream = torch.cuda.Stream(device)
-        copied = [torch.cuda.Event() for _ in range(2)]
-        consumed = [None, None]
+        copied = [torch.cuda.Event() for _ in range(3)]
+        consumed = [None, None, None]
         t_first = torch.cuda.Event(enable_timing=True)
         t_last = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(device)
         for k in range(args.warmup + steps):
-            j = k % 2
+            j = k % 3
+            if k == args.warmup:
+                # the warm-up steps drain first, so that the timed window holds exactly the timed steps
+                # (their first copy is then not overlapped: the pipeline fills inside the window)
+                torch.cuda.synchronize(device)
+                t_first.record(cstream)
             if consumed[j] is not None:
                 cstream.wait_event(consumed[j])
-            if k == args.warmup:
-                t_first.record(cstream)
             with torch.cuda.stream(cstream):
                 dv[j].copy_(hv, non_blocking=True)
             copied[j].record(cstream)
@@ -398,12 +402,12 @@ def run_workload(args, w, rank, world, device, *, refine: int, sec3: bool, wedge
             consumed[j].record(stream)
             ascend()
             rescore()
-            hq[j].copy_(quat, non_blocking=True)
-            hs[j].copy_(score, non_blocking=True)
+            hq[k % 2].copy_(quat, non_blocking=True)
+            hs[k % 2].copy_(score, non_blocking=True)
         t_last.record(stream)
         torch.cuda.synchronize(device)
         e2e_ms = replicas.max_over_ranks([t_first.elapsed_time(t_last)], device)[0]
-        del dv[1]
+        del dv[1:]
         progress(f"{w.name} {name}: timed {t_tot / steps:.2f} ms/step, e2e {e2e_ms / steps:.2f} ms/step")
         sec3_res = sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device, sec3_starts, refine) if (
             name == "bf16split" and sec3) else None
@@ -632,7 +636,8 @@ def sec3_leg(args, w, plan, tmpl, vols, coeffs, stream, flush, device, S: int, r
             "config": {"grid": f"super-Fibonacci {n_grid} rotations, neighbour radius {args.sec3_radius:g} deg",
                        "candidate_band": w.stages[0], "candidates": S, "newton_steps_per_band": args.sec3_steps,
                        "bands": w.stages, "fp64_rescore_top_k": min(refine, S),
-                       "newton_lanes_per_start": tune["newton_group"] if tune else "default"},
+                       "newton_lanes_per_start": tune["newton_group"] if tune else "default",
+                       "newton_orbit_dealing": ({1: "row", 2: "flat"}.get(tune["newton_dealing"]) if tune else "row")},
             "gpu_launches_per_step": 3 * math.ceil(B / min(B, 4096)) + 3 + 1 + (1 if min(refine, S) else 0)}
 
 

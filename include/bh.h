@@ -269,8 +269,9 @@ typedef struct {
   int dealing;            /* how a group's lanes share the orbits (m, n) of an evaluation: 0 = autotuned
                              (by rows when not tuned), 1 = row by row (lane q takes n = q - m + kG of row m),
                              2 = flat across rows (orbit m^2 + m + n to lane (m^2 + m + n) mod G; no lanes
-                             idle at row ends; group 4, 8 or 16, starts_per_thread 1 or 2).  Gradient ascent
-                             only; results differ between dealings by FP32 rounding */
+                             idle at row ends; gradient ascent: group 4, 8 or 16, starts_per_thread 1 or
+                             2; Newton steps: group 8, 16 or 32).  Not for the constrained ascent; results
+                             differ between dealings by FP32 rounding */
   const int* stage_table;  /* device, B * BH_STAGE_ROW ints or NULL: a marching schedule per subtomogram,
                              row b = (count, band_1 < band_2 < ...), e.g. from bh_choose_bands.  `stages`
                              then gives the largest band any row may use (shared memory, kernel variant)
@@ -433,10 +434,11 @@ typedef struct {
 int bh_autotune(bh_plan* plan, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out);
 
 /*
- * Time the Newton kernel (opts.newton) with 1, 2, 4, 8, 16 and 32 lanes per start for this shape and keep
- * the fastest in the plan for (band stages[nstages-1], S); bh_align_batch with opts.newton and group 0
- * uses it.  out (may be NULL) receives align_group and align_ms; the other fields are zero.  Synchronous;
- * allocates and frees its own scratch.
+ * Time the Newton kernel (opts.newton) with 1, 2, 4, 8, 16 and 32 lanes per start dealt by rows and 8, 16
+ * and 32 dealt in flat order for this shape, and keep the fastest in the plan for (band stages[nstages-1],
+ * S); bh_align_batch with opts.newton and group 0 uses it.  out (may be NULL) receives align_group,
+ * align_dealing and align_ms; align_starts_per_thread is 1, the other fields zero.  Synchronous; allocates
+ * and frees its own scratch.
  */
 int bh_autotune_newton(bh_plan* plan, int B, int S, const int* stages, int nstages, int steps, bh_tune_result* out);
 

@@ -494,12 +494,12 @@ def bh_autotune(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
 
 
 def bh_autotune_newton(plan: Plan, B: int, S: int, stages, steps: int) -> dict:
-    """Time the Newton kernel's lanes per start for this shape and keep the fastest in the plan."""
+    """Time the Newton kernel's lanes per start and orbit dealings for this shape and keep the fastest in the plan."""
     st = (ctypes.c_int * len(stages))(*[int(x) for x in stages])
     r = TuneResult()
     _check(lib().bh_autotune_newton(plan.handle, B, S, st, len(stages), steps, ctypes.byref(r)),
            "bh_autotune_newton")
-    return {"newton_group": r.align_group, "newton_ms": r.align_ms}
+    return {"newton_group": r.align_group, "newton_dealing": r.align_dealing, "newton_ms": r.align_ms}
 
 
 class ServeOpts(ctypes.Structure):

@@ -594,6 +594,73 @@ struct EvalH {
   float hxx, hxy, hxz, hyy, hyz, hzz;  // symmetric body-frame Hessian
 };
 
+// The Hessian evaluations' common end: the group's sums over its G lanes, then the body-frame gradient and
+// the symmetrised body-frame Hessian from the Euler-angle sums (S, its first derivatives Sa, Sb, Sg, the second
+// ones Saa, Sab, Sag, Sbg, Sgg, and Sk, SL for the second beta derivative).
+template <int G>
+__device__ EvalH finish_hess(float S, float Sa, float Sb, float Sg, float Saa, float Sab, float Sag, float Sbg,
+                             float Sgg, float Sk, float SL, float2 es, float2 ed, float xb, float sinb) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    S += __shfl_xor_sync(0xffffffffu, S, o);
+    Sa += __shfl_xor_sync(0xffffffffu, Sa, o);
+    Sb += __shfl_xor_sync(0xffffffffu, Sb, o);
+    Sg += __shfl_xor_sync(0xffffffffu, Sg, o);
+    Saa += __shfl_xor_sync(0xffffffffu, Saa, o);
+    Sab += __shfl_xor_sync(0xffffffffu, Sab, o);
+    Sag += __shfl_xor_sync(0xffffffffu, Sag, o);
+    Sbg += __shfl_xor_sync(0xffffffffu, Sbg, o);
+    Sgg += __shfl_xor_sync(0xffffffffu, Sgg, o);
+    Sk += __shfl_xor_sync(0xffffffffu, Sk, o);
+    SL += __shfl_xor_sync(0xffffffffu, SL, o);
+  }
+  const float2 eg = cmul(es, cconj(ed));  // (cos gamma, sin gamma)
+  const float cG = eg.x, sG = eg.y;
+  EvalH r;
+  r.S = S;
+  if (!(sinb > 1e-4f)) {  // Euler chart singular: gradient only along gamma, no curvature information
+    const float Q = 0.f;
+    r.gx = Sb * sG + Q * cG;
+    r.gy = Sb * cG - Q * sG;
+    r.gz = Sg;
+    r.hxx = r.hxy = r.hxz = r.hyy = r.hyz = r.hzz = 0.f;
+    return r;
+  }
+  const float isb = 1.f / sinb, isb2 = isb * isb;
+  const float Q = (xb * Sg - Sa) * isb;
+  r.gx = Sb * sG + Q * cG;
+  r.gy = Sb * cG - Q * sG;
+  r.gz = Sg;
+  const float Sbb = -xb * isb * Sb + Sk * isb2 - SL;
+  // X_i = v_i . (d_alpha, d_beta, d_gamma); X_i X_j S = v_i^T E v_j + (b_i d_beta v_j + c_i d_gamma v_j) . grad
+  const float v[3][3] = {{-cG * isb, sG, xb * cG * isb}, {sG * isb, cG, -xb * sG * isb}, {0.f, 0.f, 1.f}};
+  const float dbv[3][3] = {{cG * xb * isb2, 0.f, -cG * isb2}, {-sG * xb * isb2, 0.f, sG * isb2}, {0.f, 0.f, 0.f}};
+  const float dgv[3][3] = {{v[1][0], v[1][1], v[1][2]}, {-v[0][0], -v[0][1], -v[0][2]}, {0.f, 0.f, 0.f}};
+  const float E[3][3] = {{Saa, Sab, Sag}, {Sab, Sbb, Sbg}, {Sag, Sbg, Sgg}};
+  const float gr[3] = {Sa, Sb, Sg};
+  float XX[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float Ev[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Ev[k] = E[k][0] * v[i][0] + E[k][1] * v[i][1] + E[k][2] * v[i][2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float t = v[j][0] * Ev[0] + v[j][1] * Ev[1] + v[j][2] * Ev[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) t = fmaf(v[i][1] * dbv[j][k] + v[i][2] * dgv[j][k], gr[k], t);
+      XX[i][j] = t;
+    }
+  }
+  r.hxx = XX[0][0];
+  r.hyy = XX[1][1];
+  r.hzz = XX[2][2];
+  r.hxy = 0.5f * (XX[0][1] + XX[1][0]);
+  r.hxz = 0.5f * (XX[0][2] + XX[2][0]);
+  r.hyz = 0.5f * (XX[1][2] + XX[2][1]);
+  return r;
+}
+
 // Score, body-frame gradient and Hessian (FP32) of one rotation at band L (Newton steps, Sec. III).  The
 // evaluation follows eval_rotations with C = 1 and adds the second Euler-angle derivatives: along alpha and
 // gamma the orbit terms only pick up factors of m and n; the second beta derivative comes from the Wigner
@@ -692,65 +759,121 @@ __device__ EvalH eval_hess(const float4* __restrict__ tab, int Lb, int L, float4
     SL += hL;
     Wrow = cmul(Wrow, Ed2);
   }
-#pragma unroll
-  for (int o = 1; o < G; o <<= 1) {
-    S += __shfl_xor_sync(0xffffffffu, S, o);
-    Sa += __shfl_xor_sync(0xffffffffu, Sa, o);
-    Sb += __shfl_xor_sync(0xffffffffu, Sb, o);
-    Sg += __shfl_xor_sync(0xffffffffu, Sg, o);
-    Saa += __shfl_xor_sync(0xffffffffu, Saa, o);
-    Sab += __shfl_xor_sync(0xffffffffu, Sab, o);
-    Sag += __shfl_xor_sync(0xffffffffu, Sag, o);
-    Sbg += __shfl_xor_sync(0xffffffffu, Sbg, o);
-    Sgg += __shfl_xor_sync(0xffffffffu, Sgg, o);
-    Sk += __shfl_xor_sync(0xffffffffu, Sk, o);
-    SL += __shfl_xor_sync(0xffffffffu, SL, o);
+  return finish_hess<G>(S, Sa, Sb, Sg, Saa, Sab, Sag, Sbg, Sgg, Sk, SL, es, ed, xb, sinb);
+}
+
+// eval_hess with the orbits dealt in flat order across rows (as eval_flat, one start per group): orbit
+// o = m^2 + m + n goes to lane o mod G, a round of G orbits runs one l-loop from its lowest row with each lane's
+// seed injected at its own l = m, and the lane's phases follow it from orbit to orbit.  The Euler-angle sums
+// are accumulated per orbit with the orbit's own (m, n) factors (eval_hess adds them per row first), so the
+// two differ by rounding only.
+template <int G>
+__device__ EvalH eval_hess_flat(const float4* __restrict__ tab, int Lb, int L, float4 q, int qg,
+                                const float* __restrict__ lbin) {
+  const float w = q.x, x = q.y, y = q.z, z = q.w;
+  const float cb = sqrtf(w * w + z * z), sb = sqrtf(x * x + y * y);
+  const float2 es = cb > 0.f ? make_float2(w / cb, z / cb) : make_float2(1.f, 0.f);
+  const float2 ed = sb > 0.f ? make_float2(y / sb, -x / sb) : make_float2(1.f, 0.f);
+  const float xb = (cb - sb) * (cb + sb), sinb = 2.f * cb * sb;
+  const float cbc = fmaxf(cb, 1e-30f), sbc = fmaxf(sb, 1e-30f);
+  const float lcc = log2f(cbc), lss = log2f(sbc), rcs = cbc / sbc, rsc = sbc / cbc;
+  const float2 Es = cconj(es), Ed = cconj(ed);
+  const float2 EsG = cpow(Es, G), edG = cpow(ed, G);
+  const float2 R1 = cmul(EsG, edG), R2 = cmul(EsG, cconj(edG));
+  const float2 eig = cmul(es, Ed), eia = cmul(es, ed);  // e^{i gamma}, e^{i alpha}
+  const float2 E2g = cmul(eig, eig), E2a = cmul(eia, eia);
+  const int norb = (L + 1) * (L + 1);
+  int m = orbit_row(qg), n = qg - m * m - m;  // the lane's orbit (m, n); it is live while m <= L
+  int rowbase = tab_base(m, Lb);
+  const float2 pa = cpow_bin(Es, m + n);
+  float2 P1 = cmul(pa, cpow_bin(Ed, m - n)), P2 = cmul(pa, cpow_bin(ed, m - n));
+  float2 U1 = cmul(cmul(Ed, Ed), cpow_bin(eig, 2 * m + 1)), U2 = cmul(cmul(ed, ed), cpow_bin(eia, 2 * m + 1));
+  float S = 0.f, Sa = 0.f, Sb = 0.f, Sg = 0.f;
+  float Saa = 0.f, Sab = 0.f, Sag = 0.f, Sbg = 0.f, Sgg = 0.f, Sk = 0.f, SL = 0.f;
+  int m_lo = 0, m_hi = 0;  // rows of the round's first and last orbits (the same for every lane)
+  for (int c0 = 0; c0 < norb; c0 += G) {
+    while ((m_lo + 1) * (m_lo + 1) <= c0) ++m_lo;
+    const int last = min(c0 + G, norb) - 1;
+    while ((m_hi + 1) * (m_hi + 1) <= last) ++m_hi;
+    const bool live = m <= L;
+    const int wl = live ? 2 * m + 1 : 0;
+    const float4* ep0 = tab + (live ? rowbase + (n + m) : 0);
+    const float lb = live ? __ldg(lbin + m * kBinStride + m + n) : 0.f;
+    const float fa = (float)(m + n), fd = (float)(m - n), fn = (float)n, fm = (float)m;
+    const float mn = (float)(m * n), fm2 = (float)(m * m), fn2 = (float)(n * n);
+    const float sq2 = fm2 + fn2, pq2 = fm2 * fn2;
+    float d = live ? exp2f(lb + fa * lcc + fd * lss) : 0.f;
+    d = ((m - n) & 1) ? -d : d;
+    const float dp = 0.5f * d * (fd * rcs - fa * rsc);
+    float e1 = 0.f, e2 = 0.f, p1 = 0.f, p2 = 0.f;
+    float a1r = 0.f, a1i = 0.f, a2r = 0.f, a2i = 0.f, b1r = 0.f, b1i = 0.f, b2r = 0.f, b2i = 0.f;
+    float q1r = 0.f, q1i = 0.f, q2r = 0.f, q2i = 0.f;
+#define BH_HSTEP(X, K, G_, INJECT)                                                           \
+  {                                                                                          \
+    const float t_ = fmaf(-mn, (K).x, xb);                                                   \
+    float en = fmaf(t_, e1, -(G_) * e2);                                                     \
+    float pn = fmaf(t_, p1, -fmaf(sinb, e1, (G_) * p2));                                     \
+    if (INJECT) {                                                                            \
+      en = (l == m) ? d : en;                                                                \
+      pn = (l == m) ? dp : pn;                                                               \
+    }                                                                                        \
+    a1r = fmaf(en, (X).x, a1r); a1i = fmaf(en, (X).y, a1i);                                  \
+    a2r = fmaf(en, (X).z, a2r); a2i = fmaf(en, (X).w, a2i);                                  \
+    b1r = fmaf(pn, (X).x, b1r); b1i = fmaf(pn, (X).y, b1i);                                  \
+    b2r = fmaf(pn, (X).z, b2r); b2i = fmaf(pn, (X).w, b2i);                                  \
+    const float el = (K).w * en;                                                             \
+    q1r = fmaf(el, (X).x, q1r); q1i = fmaf(el, (X).y, q1i);                                  \
+    q2r = fmaf(el, (X).z, q2r); q2i = fmaf(el, (X).w, q2i);                                  \
+    e2 = e1; e1 = en; p2 = p1; p1 = pn;                                                      \
   }
-  const float2 eg = cmul(es, cconj(ed));  // (cos gamma, sin gamma)
-  const float cG = eg.x, sG = eg.y;
-  EvalH r;
-  r.S = S;
-  if (!(sinb > 1e-4f)) {  // Euler chart singular: gradient only along gamma, no curvature information
-    const float Q = 0.f;
-    r.gx = Sb * sG + Q * cG;
-    r.gy = Sb * cG - Q * sG;
-    r.gz = Sg;
-    r.hxx = r.hxy = r.hxz = r.hyy = r.hyz = r.hzz = 0.f;
-    return r;
-  }
-  const float isb = 1.f / sinb, isb2 = isb * isb;
-  const float Q = (xb * Sg - Sa) * isb;
-  r.gx = Sb * sG + Q * cG;
-  r.gy = Sb * cG - Q * sG;
-  r.gz = Sg;
-  const float Sbb = -xb * isb * Sb + Sk * isb2 - SL;
-  // X_i = v_i . (d_alpha, d_beta, d_gamma); X_i X_j S = v_i^T E v_j + (b_i d_beta v_j + c_i d_gamma v_j) . grad
-  const float v[3][3] = {{-cG * isb, sG, xb * cG * isb}, {sG * isb, cG, -xb * sG * isb}, {0.f, 0.f, 1.f}};
-  const float dbv[3][3] = {{cG * xb * isb2, 0.f, -cG * isb2}, {-sG * xb * isb2, 0.f, sG * isb2}, {0.f, 0.f, 0.f}};
-  const float dgv[3][3] = {{v[1][0], v[1][1], v[1][2]}, {-v[0][0], -v[0][1], -v[0][2]}, {0.f, 0.f, 0.f}};
-  const float E[3][3] = {{Saa, Sab, Sag}, {Sab, Sbb, Sbg}, {Sag, Sbg, Sgg}};
-  const float gr[3] = {Sa, Sb, Sg};
-  float XX[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float Ev[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) Ev[k] = E[k][0] * v[i][0] + E[k][1] * v[i][1] + E[k][2] * v[i][2];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float t = v[j][0] * Ev[0] + v[j][1] * Ev[1] + v[j][2] * Ev[2];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) t = fmaf(v[i][1] * dbv[j][k] + v[i][2] * dgv[j][k], gr[k], t);
-      XX[i][j] = t;
+    // l = m_lo .. m_hi: each lane's orbit starts at its own row m (seed injected there; zeros before)
+    for (int l = m_lo; l <= m_hi; ++l) {
+      const float4 X = ep0[(max(l, m) - m) * wl];
+      const float4 k0 = c_ecoef[l];
+      const float g0 = gcoef(k0, sq2, pq2);
+      BH_HSTEP(X, k0, g0, true);
+    }
+    // l = m_hi+1 .. L: every live lane is inside its orbit
+    const float4* ep = ep0 + (m_hi + 1 - m) * wl;
+    for (int l = m_hi + 1; l <= L; ++l) {
+      const float4 X = *ep;
+      ep += wl;
+      const float4 k0 = c_ecoef[l];
+      const float g0 = gcoef(k0, sq2, pq2);
+      BH_HSTEP(X, k0, g0, false);
+    }
+#undef BH_HSTEP
+    const float z1r = P1.x * a1r - P1.y * a1i, z1i = P1.x * a1i + P1.y * a1r;
+    const float z2r = P2.x * a2r - P2.y * a2i, z2i = P2.x * a2i + P2.y * a2r;
+    const float y1r = P1.x * b1r - P1.y * b1i, y1i = P1.x * b1i + P1.y * b1r;
+    const float y2r = P2.x * b2r - P2.y * b2i, y2i = P2.x * b2i + P2.y * b2r;
+    const float zr = z1r + z2r;
+    S += zr;
+    Sa = fmaf(fm, z1i, fmaf(fn, z2i, Sa));
+    Sg = fmaf(fn, z1i, fmaf(fm, z2i, Sg));
+    Sb += y1r + y2r;
+    Saa -= fmaf(fm2, z1r, fn2 * z2r);
+    Sgg -= fmaf(fn2, z1r, fm2 * z2r);
+    Sag = fmaf(-mn, zr, Sag);
+    Sab = fmaf(fm, y1i, fmaf(fn, y2i, Sab));
+    Sbg = fmaf(fn, y1i, fmaf(fm, y2i, Sbg));
+    Sk = fmaf(fmaf(-2.f * xb, mn, sq2), zr, Sk);
+    SL += (P1.x * q1r - P1.y * q1i) + (P2.x * q2r - P2.y * q2i);
+    // the lane's next orbit, G further in flat order (as in eval_flat)
+    n += G;
+    P1 = cmul(P1, R1);
+    P2 = cmul(P2, R2);
+    while (n > m) {
+      n -= 2 * m + 2;
+      rowbase += (2 * m + 1) * (Lb - m + 1);
+      ++m;
+      P1 = cmul(P1, U1);
+      P2 = cmul(P2, U2);
+      U1 = cmul(U1, E2g);
+      U2 = cmul(U2, E2a);
     }
   }
-  r.hxx = XX[0][0];
-  r.hyy = XX[1][1];
-  r.hzz = XX[2][2];
-  r.hxy = 0.5f * (XX[0][1] + XX[1][0]);
-  r.hxz = 0.5f * (XX[0][2] + XX[2][0]);
-  r.hyz = 0.5f * (XX[1][2] + XX[2][1]);
-  return r;
+  return finish_hess<G>(S, Sa, Sb, Sg, Saa, Sab, Sag, Sbg, Sgg, Sk, SL, es, ed, xb, sinb);
 }
 
 __device__ __forceinline__ const float2* template_row(const AlignArgs& a, int p) {
@@ -953,8 +1076,9 @@ __device__ __forceinline__ float newton_dir(const EvalH& e, float gn, float h0, 
   return dn;
 }
 
-// Damped Newton iteration with frequency marching (Sec. III); one CTA per subtomogram, NT = roundup(S*G, 32).
-template <int G, int NT>
+// Damped Newton iteration with frequency marching (Sec. III); one CTA per subtomogram, NT = roundup(S*G, 32);
+// the orbits dealt by rows (D = 1, eval_hess) or in flat order (D = 2, eval_hess_flat).
+template <int G, int NT, int D>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_newton(const AlignArgs a) {
   extern __shared__ float4 smem_tab[];
   const int p = blockIdx.x;
@@ -974,7 +1098,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_newton(const AlignArgs a
     const int L = sched[1 + st];
     const float hmax = 3.14159265358979f / (float)L, h0 = 0.5f * hmax;
     float lam = 1.f;
-    cur = eval_hess<G>(smem_tab, Lb, L, q, qg, a.lbin);
+    cur = D == 2 ? eval_hess_flat<G>(smem_tab, Lb, L, q, qg, a.lbin) : eval_hess<G>(smem_tab, Lb, L, q, qg, a.lbin);
     for (int t = 0; t < a.steps; ++t) {
       const float gn = sqrtf(cur.gx * cur.gx + cur.gy * cur.gy + cur.gz * cur.gz);
       const bool stop = !(gn > 1e-12f * fabsf(cur.S));
@@ -986,7 +1110,8 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_newton(const AlignArgs a
       sincosf(stop ? 0.f : 0.5f * dn, &sh, &ch);
       const float4 dq = make_float4(ch, sh * d[0] * inv, sh * d[1] * inv, sh * d[2] * inv);
       const float4 qt = qnormalize(qmul(q, dq));
-      const EvalH tr = eval_hess<G>(smem_tab, Lb, L, qt, qg, a.lbin);
+      const EvalH tr =
+          D == 2 ? eval_hess_flat<G>(smem_tab, Lb, L, qt, qg, a.lbin) : eval_hess<G>(smem_tab, Lb, L, qt, qg, a.lbin);
       if (!stop) {
         if (tr.S > cur.S) {
           q = qt;
@@ -1431,23 +1556,29 @@ __device__ __forceinline__ Rot64 rot64(float4 qf) {
   return r;
 }
 
-// v (FP64) as hi + lo with hi, lo FP32: hi keeps the sign, exponent and leading 24 significand bits of v
-// (truncation, formed with integer operations), lo the same of the exact remainder v - hi, so that
-// |v - hi - lo| <= 2^-46 |v|.  Values outside the FP32 normal range (|v| < 2^-126 or >= 2^128) give
-// hi = lo = 0.  Costs one FP64 subtraction; the conversions run on the integer pipe, not the FP64 one.
-__device__ __forceinline__ float trunc_float(double v, double* vt) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned int h = (unsigned int)(b >> 32);
-  const int e = (int)((h >> 20) & 0x7FFu) - 896;  // FP32 biased exponent
-  const bool ok = e > 0 && e < 255;
-  const unsigned int fb = (h & 0x80000000u) | ((unsigned int)e << 23) | ((h & 0xFFFFFu) << 3) | ((unsigned int)b >> 29);
-  *vt = ok ? __longlong_as_double((long long)(b & 0xFFFFFFFFE0000000ull)) : 0.0;
-  return ok ? __uint_as_float(fb) : 0.f;
-}
+// v (FP64) as hi + lo with hi, lo FP32, formed with integer operations (no FP64 instruction): hi keeps the
+// sign, exponent and leading 24 significand bits of v (truncation); lo is the remaining 29 significand bits
+// of v as an integer, converted to FP32 (rounded to 24 bits) and scaled by their place value, so that
+// |v - hi - lo| <= 2^-48 |v|.  hi = lo = 0 for |v| < 2^-74 (lo's scale would leave the FP32 normal range;
+// such terms are below 2^-74 of a table entry), and for values at or above 2^128 (not reached).
 __device__ __forceinline__ void split64(double v, float& hi, float& lo) {
-  double vh, vl;
-  hi = trunc_float(v, &vh);
-  lo = trunc_float(v - vh, &vl);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int h = (unsigned int)(b >> 32), sgn = h & 0x80000000u;
+  const int E = (int)((h >> 20) & 0x7FFu);  // FP64 biased exponent: |v| in [2^(E-1023), 2^(E-1022))
+  const bool ok = E >= 949 && E < 1151;     // 2^-74 <= |v| < 2^128
+  const unsigned int fb = sgn | ((unsigned int)(E - 896) << 23) | ((h & 0xFFFFFu) << 3) | ((unsigned int)b >> 29);
+  const float r = (float)((unsigned int)b & 0x1FFFFFFFu);       // the low 29 significand bits, < 2^29
+  const float scale = __uint_as_float(sgn | ((unsigned int)(E - 948) << 23));  // +-2^(E - 1075), normal
+  hi = ok ? __uint_as_float(fb) : 0.f;
+  lo = ok ? r * scale : 0.f;
+}
+// FP32 to FP64 by integer operations (FP32 subnormals, below 2^-126, give 0).
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return e ? __longlong_as_double((long long)b) : 0.0;
 }
 // s + c += (hi + lo) x, compensated: hi x is split exactly into p + pe (FMA), p is added to s with an
 // error-free two-sum, and the two-sum's error, pe and lo x go to the correction c.
@@ -1488,7 +1619,7 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
       const float4* ep = rowp + (n + m);
       const double2* kp = crow + (n + m);
       // the chain's sums a = sum_l e^l x^l: the recursion in FP64, each term accumulated in compensated FP32
-      // (s + c; the split of e^l loses 2^-46 of it, the sum about 2^-43 of the terms' magnitudes, far below the
+      // (s + c; the split of e^l loses 2^-48 of it, the sum about 2^-43 of the terms' magnitudes, far below the
       // table's FP32 rounding), without FP64 conversions and multiply-adds of the FP32 table entries
       float4 xv = *ep;
       float s1r, s1i, s2r, s2i, c1r = 0.f, c1i = 0.f, c2r = 0.f, c2i = 0.f;
@@ -1517,8 +1648,8 @@ __device__ double score_rotation64(const float4* __restrict__ tab, int Lb, int L
         acc_ff(s2r, c2r, hi, lo, xv.z);
         acc_ff(s2i, c2i, hi, lo, xv.w);
       }
-      const double a1r = (double)s1r + (double)c1r, a1i = (double)s1i + (double)c1i;
-      const double a2r = (double)s2r + (double)c2r, a2i = (double)s2i + (double)c2i;
+      const double a1r = f2d(s1r) + f2d(c1r), a1i = f2d(s1i) + f2d(c1i);
+      const double a2r = f2d(s2r) + f2d(c2r), a2i = f2d(s2i) + f2d(c2i);
       S += (P1.x * a1r - P1.y * a1i) + (P2.x * a2r - P2.y * a2i);
       P1 = cm64(P1, R1);
       P2 = cm64(P2, R2);
@@ -1743,17 +1874,17 @@ int launch_align(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t
   }
 }
 
-template <int G, int NT>
+template <int G, int NT, int D>
 int launch_newton_nt(const AlignArgs& a, size_t smem, cudaStream_t stream) {
   static SmemAttr have;
-  int st = ensure_smem(k_newton<G, NT>, have, smem);
+  int st = ensure_smem(k_newton<G, NT, D>, have, smem);
   if (st != BH_OK) return st;
-  k_newton<G, NT><<<a.B, NT, smem, stream>>>(a);
+  k_newton<G, NT, D><<<a.B, NT, smem, stream>>>(a);
   BH_CHECK_LAUNCH();
   return BH_OK;
 }
 
-template <int G>
+template <int G, int D>
 int launch_newton_g(const AlignArgs& a, bool score_only, int L, cudaStream_t stream) {
   const int threads = round_up(a.S * G, 32);
   const size_t sel = (size_t)((a.S + 3) & ~3) * sizeof(float) + (size_t)a.S * sizeof(float4);
@@ -1768,27 +1899,36 @@ int launch_newton_g(const AlignArgs& a, bool score_only, int L, cudaStream_t str
     return BH_OK;
   }
   switch (threads) {
-    case 32: return launch_newton_nt<G, 32>(a, smem, stream);
-    case 64: return launch_newton_nt<G, 64>(a, smem, stream);
+    case 32: return launch_newton_nt<G, 32, D>(a, smem, stream);
+    case 64: return launch_newton_nt<G, 64, D>(a, smem, stream);
     case 96:
-    case 128: return launch_newton_nt<G, 128>(a, smem, stream);
+    case 128: return launch_newton_nt<G, 128, D>(a, smem, stream);
     case 160:
     case 192:
     case 224:
-    case 256: return launch_newton_nt<G, 256>(a, smem, stream);
-    default: return launch_newton_nt<G, 512>(a, smem, stream);
+    case 256: return launch_newton_nt<G, 256, D>(a, smem, stream);
+    default: return launch_newton_nt<G, 512, D>(a, smem, stream);
   }
 }
 
-// Newton iteration (or, score_only, the score/gradient/Hessian evaluation at band L) with G lanes per start.
-int launch_newton(const AlignArgs& a, int G, bool score_only, int L, cudaStream_t stream) {
+// Newton iteration (or, score_only, the score/gradient/Hessian evaluation at band L, always row-dealt) with G
+// lanes per start; D = 1 deals the orbits by rows, D = 2 in flat order (G in {8, 16, 32}).
+int launch_newton(const AlignArgs& a, int G, int D, bool score_only, int L, cudaStream_t stream) {
+  if (D == 2 && !score_only) {
+    switch (G) {
+      case 8: return launch_newton_g<8, 2>(a, false, L, stream);
+      case 16: return launch_newton_g<16, 2>(a, false, L, stream);
+      case 32: return launch_newton_g<32, 2>(a, false, L, stream);
+      default: return fail(BH_ERR_ARG, "flat dealing of the Newton kernel: group %d not in {8,16,32}", G);
+    }
+  }
   switch (G) {
-    case 1: return launch_newton_g<1>(a, score_only, L, stream);
-    case 2: return launch_newton_g<2>(a, score_only, L, stream);
-    case 4: return launch_newton_g<4>(a, score_only, L, stream);
-    case 8: return launch_newton_g<8>(a, score_only, L, stream);
-    case 16: return launch_newton_g<16>(a, score_only, L, stream);
-    case 32: return launch_newton_g<32>(a, score_only, L, stream);
+    case 1: return launch_newton_g<1, 1>(a, score_only, L, stream);
+    case 2: return launch_newton_g<2, 1>(a, score_only, L, stream);
+    case 4: return launch_newton_g<4, 1>(a, score_only, L, stream);
+    case 8: return launch_newton_g<8, 1>(a, score_only, L, stream);
+    case 16: return launch_newton_g<16, 1>(a, score_only, L, stream);
+    case 32: return launch_newton_g<32, 1>(a, score_only, L, stream);
     default: return fail(BH_ERR_ARG, "group %d not in {1,2,4,8,16,32}", G);
   }
 }
@@ -1968,7 +2108,7 @@ extern "C" int bh_score_hess(const bh_plan* p, const float* tmpl, const float* s
   a.score_out = score;
   a.grad_out = grad;
   a.hess_out = hess;
-  return launch_newton(a, default_group(S, L), true, L, static_cast<cudaStream_t>(stream));
+  return launch_newton(a, default_group(S, L), 1, true, L, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int bh_wedge_norm(const bh_plan* p, const bh_wedge* w, const float* quats, int S, int L, float* dn,
@@ -2071,13 +2211,20 @@ extern "C" int bh_align_batch(const bh_plan* p, const float* tmpl, const float* 
     st = launch_wedge(a, w, G, static_cast<cudaStream_t>(stream));
   } else if (opts && opts->newton) {
     if (opts->starts_per_thread > 1) return fail(BH_ERR_ARG, "Newton steps run one start per thread group");
+    int DN = opts->dealing;
     if (opts->group == 0) {
       auto it = p->newton_group.find({a.Lb, S});
-      G = it != p->newton_group.end() ? it->second : default_group_newton(S, a.Lb);
+      if (it != p->newton_group.end()) {
+        G = it->second.group;
+        if (DN == 0) DN = it->second.dealing;
+      } else {
+        G = default_group_newton(S, a.Lb);
+      }
     }
+    if (DN == 0) DN = 1;
     if (round_up(S * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S*group = %d exceeds %d threads", S * G, kMaxThreads);
-    st = launch_newton(a, G, false, 0, static_cast<cudaStream_t>(stream));
+    st = launch_newton(a, G, DN, false, 0, static_cast<cudaStream_t>(stream));
   } else if (D == 2) {
     if (round_up((S / C) * G, 32) > kMaxThreads)
       return fail(BH_ERR_ARG, "S/%d*group = %d exceeds %d threads", C, (S / C) * G, kMaxThreads);
@@ -2285,12 +2432,18 @@ extern "C" int bh_autotune_newton(bh_plan* p, int B, int S, const int* stages, i
   if (e == cudaSuccess) e = cudaMemsetAsync(tmpl, 0x3C, (size_t)p->Nb * 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(starts, 0x3C, (size_t)B * S * 16, st);
   if (e != cudaSuccess) return cuda_fail(e, "autotune setup");
-  int best_g = 0;
+  int best_g = 0, best_d = 1;
   float best_ms = 1e30f;
-  for (int G : {1, 2, 4, 8, 16, 32}) {
+  struct Cand {
+    int G, D;
+  };
+  for (const Cand c : {Cand{1, 1}, Cand{2, 1}, Cand{4, 1}, Cand{8, 1}, Cand{16, 1}, Cand{32, 1}, Cand{8, 2},
+                       Cand{16, 2}, Cand{32, 2}}) {
+    const int G = c.G;
     if (round_up(S * G, 32) > kMaxThreads) continue;
     bh_align_opts o{};
     o.group = G;
+    o.dealing = c.D;
     o.newton = 1;
     int rc = BH_OK;
     for (int it = 0; it < 2 && rc == BH_OK; ++it)
@@ -2308,15 +2461,17 @@ extern "C" int bh_autotune_newton(bh_plan* p, int B, int S, const int* stages, i
     if (ms < best_ms) {
       best_ms = ms;
       best_g = G;
+      best_d = c.D;
     }
   }
   cleanup();
   if (best_g == 0) return fail(BH_ERR_UNSUPPORTED, "no Newton variant runs for S=%d band %d", S, Lb);
-  p->newton_group[{Lb, S}] = best_g;
+  p->newton_group[{Lb, S}] = bh_plan::AlignVariant{best_g, 1, best_d};
   if (out) {
     *out = bh_tune_result{};
     out->align_group = best_g;
     out->align_starts_per_thread = 1;
+    out->align_dealing = best_d;
     out->align_ms = best_ms;
   }
   return BH_OK;

@@ -145,7 +145,7 @@ struct bh_plan {
     int group, starts_per_thread, dealing;
   };
   std::map<std::pair<int, int>, AlignVariant> align_group;  // autotuned ascent variant by (band, S)
-  std::map<std::pair<int, int>, int> newton_group;                 // autotuned lanes per start of the Newton kernel
+  std::map<std::pair<int, int>, AlignVariant> newton_group;        // autotuned Newton variant (lanes per start, dealing)
 };
 
 namespace bh {

@@ -568,3 +568,40 @@ def test_align_flat_dealing_agrees(dev, group, spt):
     agree = [math.degrees(wigner.geodesic_angle(sq[i] / np.linalg.norm(sq[i]), ref.start_q[i])) < 0.1
              for i in range(w.S)]
     assert sum(agree) >= w.S - 1
+
+
+@pytest.mark.parametrize("group", [8, 16, 32])
+def test_newton_flat_dealing_agrees(dev, group):
+    """Newton steps with the orbits dealt in flat order across rows: the oracle's Newton optimum from the same
+    starts, its score, and the oracle's final rotation of (all but at most one of) the starts."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    ref = align.align_particle(Bs, t, f, w.starts[0].astype(np.float64), w.stages, 15, method="newton")
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    q, s, sq, _ = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev),
+                                    torch.from_numpy(w.starts).to(dev), w.stages, 15, group=group, dealing=2,
+                                    newton=True, per_start=True)
+    q = q.cpu().numpy()[0].astype(np.float64)
+    assert math.degrees(wigner.geodesic_angle(q / np.linalg.norm(q), ref.q)) < 0.1
+    assert abs(float(s[0]) - ref.score) < 1e-4 * abs(ref.score)
+    sq = sq.cpu().numpy()[0].astype(np.float64)
+    agree = [math.degrees(wigner.geodesic_angle(sq[i] / np.linalg.norm(sq[i]), ref.start_q[i])) < 0.1
+             for i in range(w.S)]
+    assert sum(agree) >= w.S - 1
+
+
+def test_newton_flat_hessian_matches_row(dev):
+    """At band 8 on one subtomogram, the first Newton iteration's evaluation is the same in both dealings: a
+    zero-step run (steps = 0) returns each start's score from the flat and the row kernels within 1e-5."""
+    w = synth.make_workload("pair16")
+    Bs = basis_for(16, 8)
+    t = ball.expand(Bs, w.template.astype(np.float64))[0]
+    f = ball.expand(Bs, w.vols[0].astype(np.float64))[0]
+    p = plan_for(16, 8, bh.BH_MODE_FP32)
+    args = (p, to_f32(t).to(dev), to_f32(f[None]).to(dev), torch.from_numpy(w.starts).to(dev), [8], 0)
+    _, _, _, s_row = bh.bh_align_batch(*args, group=8, dealing=1, newton=True, per_start=True)
+    _, _, _, s_flat = bh.bh_align_batch(*args, group=8, dealing=2, newton=True, per_start=True)
+    s_row, s_flat = s_row.cpu().numpy()[0], s_flat.cpu().numpy()[0]
+    assert np.max(np.abs(s_row - s_flat)) <= 1e-5 * np.max(np.abs(s_row))
