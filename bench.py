@@ -54,7 +54,7 @@ def align_source_sha() -> str:
 # the subtomogram count (the kernel reads each subtomogram's coefficients and starts once); the figure is
 # used only while the hash matches.
 ALIGN_TRAFFIC_BYTES = {
-    ("precision64", 16, 2, 2): (195_439_360 + 3_302_144, 1024, "4202a7a2c3f49f68"),
+    ("precision64", 16, 2, 2): (194_948_352 + 3_172_352, 1024, "02f0b201936a846c"),
 }
 
 
@@ -528,9 +528,9 @@ def summarize(args, w, res, world, device) -> dict:
 
 
 def profile_align(args, device) -> dict:
-    """One ascent variant alone on a plan without the expansion table, for ncu captures: the subtomograms are
-    expanded with a full plan that is destroyed before the ascent launches, so the device holds only the
-    coefficients and starts while they run."""
+    """Ascent (or Newton) variants alone on a plan without the expansion table, for sweeps and ncu captures:
+    the subtomograms are expanded with a full plan that is destroyed before the matching launches, so the
+    device holds only the coefficients and starts while they run."""
     import torch
 
     from paper_2509_01180_gb300 import bh
@@ -550,16 +550,26 @@ def profile_align(args, device) -> dict:
     score = torch.empty((w.B,), dtype=torch.float32, device=device)
     fl = align_flops(w)
     pk, src = fp32_peak_tflops(device, measured_peaks())
-    def parse(v):  # "GxC" (row dealing) or "GxCf" (flat dealing)
+    def parse(v):  # "GxC" (row dealing) or "GxCf" (flat dealing); "nG" / "nGf": Newton steps, G lanes per start
         flat = v.endswith("f")
-        G, C = (int(x) for x in v.rstrip("f").split("x"))
-        return G, C, 2 if flat else 1
+        v = v.rstrip("f")
+        if v.startswith("n"):
+            return int(v[1:]), 1, 2 if flat else 1, True
+        G, C = (int(x) for x in v.split("x"))
+        return G, C, 2 if flat else 1, False
     variants = [parse(v) for v in args.variants.split(",")] if args.variants else \
-        [(args.group, args.starts_per_thread, args.dealing)]
+        [(args.group, args.starts_per_thread, args.dealing, False)]
+    # Newton variants start from the first 8 of each subtomogram's starts, args.sec3_steps iterations per band
+    # (the Sec. III leg's shape: 8 candidate starts at 64^3)
+    nstarts = starts[:, :8].contiguous()
     out = []
-    for G, C, D in variants:
+    for G, C, D, newton in variants:
         try:
             def run():
+                if newton:
+                    bh.bh_align_batch(plan, tmpl, coeffs, nstarts, w.stages, args.sec3_steps, quat_out=quat,
+                                      score_out=score, group=G, dealing=D, newton=True, stream=stream)
+                    return
                 bh.bh_align_batch(plan, tmpl, coeffs, starts, w.stages, w.steps, quat_out=quat, score_out=score,
                                   group=G, starts_per_thread=C, dealing=D, stream=stream)
             for _ in range(args.warmup):
@@ -571,12 +581,16 @@ def profile_align(args, device) -> dict:
                 ev[k + 1].record(stream)
             torch.cuda.synchronize(device)
         except bh.BHError as e:
-            out.append({"lanes": G, "starts_per_thread": C, "dealing": D, "error": str(e)})
+            out.append({"lanes": G, "starts_per_thread": C, "dealing": D, "newton": newton, "error": str(e)})
             continue
         ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         avg = sum(ms) / len(ms)
-        out.append({"lanes": G, "starts_per_thread": C, "dealing": "flat" if D == 2 else "row", "ms_per_launch": ms,
-                    "achieved_tflops": fl / (avg / 1e3) / 1e12, "frac": fl / (avg / 1e3) / 1e12 / pk})
+        rec = {"lanes": G, "starts_per_thread": C, "dealing": "flat" if D == 2 else "row", "ms_per_launch": ms}
+        if newton:
+            rec.update({"newton": True, "starts": 8, "steps_per_band": args.sec3_steps})
+        else:
+            rec.update({"achieved_tflops": fl / (avg / 1e3) / 1e12, "frac": fl / (avg / 1e3) / 1e12 / pk})
+        out.append(rec)
     plan.destroy()
     return {"profile": "k_align", "workload": describe(w), "flop_per_launch": fl, "peak_tflops": pk,
             "peak_source": src, "align_src_sha": align_source_sha(), "variants": out}
@@ -913,7 +927,9 @@ def main():
     ap.add_argument("--sec3-grid", type=int, default=4608, help="rotation grid size for the candidate starts")
     ap.add_argument("--sec3-radius", type=float, default=25.0, help="neighbour radius of the grid (degrees)")
     ap.add_argument("--sec3-steps", type=int, default=8, help="Newton steps per marching band")
-    ap.add_argument("--variants", default="", help="with --profile-align: lanes x starts-per-thread list, e.g. 4x2,8x1")
+    ap.add_argument("--variants", default="",
+                    help="with --profile-align: lanes x starts-per-thread list, e.g. 4x2,8x1,16x2f (f: flat dealing); "
+                         "nG / nGf: Newton steps with G lanes per start from 8 starts")
     ap.add_argument("--profile-align", action="store_true",
                     help="time one ascent variant (--group, --starts-per-thread) alone on a plan without the "
                          "expansion table; for ncu captures")
