@@ -201,7 +201,7 @@ def test_align_64_fp32_path_matches_oracle(dev):
     srt = np.sort(ref.start_score)[::-1]
     tied = (srt[0] - srt[1]) < 1e-4 * abs(srt[0])
     for kw in (dict(group=8, starts_per_thread=1, dealing=1), dict(group=16, starts_per_thread=1, dealing=2),
-               dict(group=8, starts_per_thread=2, dealing=2)):
+               dict(group=8, starts_per_thread=2, dealing=2), dict(group=16, starts_per_thread=2, dealing=2)):
         q, s = bh.bh_align_batch(p, to_f32(t).to(dev), to_f32(f[None]).to(dev),
                                  torch.from_numpy(np.ascontiguousarray(starts)).to(dev), w.stages, w.steps, **kw)
         q = q.cpu().numpy()[0].astype(np.float64)
