@@ -1518,9 +1518,9 @@ __global__ void __launch_bounds__(kBandThreads) k_choose_bands(Layout lay, const
 }
 
 // ---------------------------------------------------------------------------- FP64 re-scoring
-// The same evaluation with the d-recursion, its coefficients, the seeds, the phases and every sum in
-// FP64 (the shared-memory table stays FP32: P_l xi^l rounded once per entry).  Used to re-score the
-// best starts at the last band and select among them in FP64.
+// The same evaluation with the d-recursion, its coefficients, the seeds and the phases in FP64, each orbit's
+// chain sum in compensated FP32 pairs and the sums over orbits in FP64 (the shared-memory table stays FP32:
+// P_l xi^l rounded once per entry).  Used to re-score the best starts at the last band and select among them.
 struct Cx64 {
   double x, y;
 };
