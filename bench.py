@@ -58,7 +58,7 @@ def align_source_sha() -> str:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the ascent kernel from an ncu
 # capture, by (workload, lanes per start, starts per thread, orbit dealing): (bytes, subtomograms in the
-# captured launch, hash of align.cu the capture was taken on).  A capture of a smaller batch is scaled by
+# captured launch, source_sha of the align.cu it was taken on).  A capture of a smaller batch is scaled by
 # the subtomogram count (the kernel reads each subtomogram's coefficients and starts once); the figure is
 # used only while the hash matches.
 ALIGN_TRAFFIC_BYTES = {
