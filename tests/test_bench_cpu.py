@@ -37,3 +37,13 @@ def test_default_workload_is_the_precision_form():
     assert (N, Lmax, stages, steps, S, B) == (64, 32, [4, 8, 16, 32], 30, 32, 4096)
     # flop accounting: one evaluation at band L costs 30 flop per orbit-step and 46 per orbit
     assert bench.orbit_steps(32) == 12529 and bench.eval_flops(4) == 30 * 55 + 46 * 25
+
+
+def test_source_hash_ignores_comments_only():
+    """The stored ascent traffic figure is keyed on the alignment source without comments: a comment or
+    blank-line edit keeps the key, a code edit changes it (the bench then reports no traffic)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    code = "int f(int x) {\n  return x + 1;  // one more\n}\n"
+    assert bench.source_sha(code) == bench.source_sha("/* doc */\nint f(int x) {\n\n  return x + 1;\n}\n")
+    assert bench.source_sha(code) != bench.source_sha(code.replace("x + 1", "x + 2"))
