@@ -270,8 +270,9 @@ typedef struct {
                              (by rows when not tuned), 1 = row by row (lane q takes n = q - m + kG of row m),
                              2 = flat across rows (orbit m^2 + m + n to lane (m^2 + m + n) mod G; no lanes
                              idle at row ends; gradient ascent: group 4, 8 or 16, starts_per_thread 1 or
-                             2; Newton steps: group 8, 16 or 32).  Not for the constrained ascent; results
-                             differ between dealings by FP32 rounding */
+                             2; Newton steps: group 8, 16 or 32).  The constrained ascent (opts.wedge)
+                             deals by rows and ignores it; results differ between dealings by FP32
+                             rounding */
   const int* stage_table;  /* device, B * BH_STAGE_ROW ints or NULL: a marching schedule per subtomogram,
                              row b = (count, band_1 < band_2 < ...), e.g. from bh_choose_bands.  `stages`
                              then gives the largest band any row may use (shared memory, kernel variant)
